@@ -1,0 +1,242 @@
+"""Dictionaries, approximate dictionaries and their per-atom error bounds, in FP64.
+
+Test infrastructure only (see the package docstring).
+
+* ``DenseDict``  explicit N x K matrix (atoms are columns).
+* ``KronDict``   A~ = (sum_{r<=R} B_r (x) C_r) diag(d) evaluated with small matrix products
+                 (the SuKro structure of Section V-A), row-major vectorisation
+                 (B (x) C)[n1 N2 + n2, k1 K2 + k2] = B[n1, k1] C[n2, k2].
+* quantisers     BF16 (round to nearest even) and FP8 E4M3 with a per-atom scale
+                 s_j = max_i |a_ij| / 448, written from the formats' definitions.
+* ``Level``      one rung of the ladder {A~^i} with eps^i_j >= ||a~^i_j - a_j||_2 and RC_i
+                 (Section IV, Algorithm 1 inputs).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+EPS_SAFETY = 1e-12   # relative inflation of FP64-evaluated eps_j so that they stay upper bounds
+
+
+# ----------------------------------------------------------------------------- operators
+
+class DenseDict:
+    """Explicit dictionary; ``matvec`` / ``rmatvec`` may be restricted to an index set."""
+
+    def __init__(self, M: np.ndarray):
+        self.M = np.asarray(M, dtype=np.float64)
+        self.N, self.K = self.M.shape
+
+    def matvec(self, x, idx=None):
+        if idx is None:
+            return self.M @ x
+        return self.M[:, idx] @ x
+
+    def rmatvec(self, r, idx=None):
+        if idx is None:
+            return self.M.T @ r
+        return self.M[:, idx].T @ r
+
+    def col(self, j):
+        return self.M[:, j]
+
+    def dense(self):
+        return self.M
+
+    def atom_norms(self):
+        return np.sqrt(np.einsum("nk,nk->k", self.M, self.M))
+
+
+class KronDict:
+    """A~ = (sum_{r < R} B_r (x) C_r) diag(d) with B_r: N1 x K1, C_r: N2 x K2.
+
+    matvec:  A~ x = vec(sum_r B_r X C_r^T),  X = reshape(d * x, K1, K2)
+    rmatvec: A~^T rho = d * vec(sum_r B_r^T P C_r),  P = reshape(rho, N1, N2)
+    The structure gives no saving on a subset of atoms, so restricted products evaluate
+    all atoms and select (the worst case of eq:complexity_model_approx).
+    """
+
+    def __init__(self, Bf, Cf, d, R=None):
+        self.Bf = np.asarray(Bf, dtype=np.float64)
+        self.Cf = np.asarray(Cf, dtype=np.float64)
+        self.R = self.Bf.shape[0] if R is None else R
+        self.N1, self.K1 = self.Bf.shape[1:]
+        self.N2, self.K2 = self.Cf.shape[1:]
+        self.N, self.K = self.N1 * self.N2, self.K1 * self.K2
+        self.d = np.asarray(d, dtype=np.float64)
+
+    def matvec(self, x, idx=None):
+        full = np.zeros(self.K)
+        if idx is None:
+            full[:] = x
+        else:
+            full[idx] = x
+        X = (self.d * full).reshape(self.K1, self.K2)
+        out = np.zeros((self.N1, self.N2))
+        for r in range(self.R):
+            out += self.Bf[r] @ X @ self.Cf[r].T
+        return out.reshape(-1)
+
+    def rmatvec(self, rho, idx=None):
+        P = np.asarray(rho, dtype=np.float64).reshape(self.N1, self.N2)
+        G = np.zeros((self.K1, self.K2))
+        for r in range(self.R):
+            G += self.Bf[r].T @ P @ self.Cf[r]
+        g = self.d * G.reshape(-1)
+        return g if idx is None else g[idx]
+
+    def col(self, j):
+        k1, k2 = divmod(int(j), self.K2)
+        c = np.zeros(self.N)
+        for r in range(self.R):
+            c += np.kron(self.Bf[r][:, k1], self.Cf[r][:, k2])
+        return self.d[j] * c
+
+    def dense(self):
+        M = np.zeros((self.N, self.K))
+        for r in range(self.R):
+            M += np.kron(self.Bf[r], self.Cf[r])
+        return M * self.d[None, :]
+
+    def atom_norms(self):
+        return np.array([np.linalg.norm(self.col(j)) for j in range(self.K)])
+
+
+def kron_unit_scale(Bf, Cf, R=None) -> np.ndarray:
+    """d_j = 1 / ||(sum_r B_r (x) C_r) e_j||_2, from the explicit columns (np.kron)."""
+    op = KronDict(Bf, Cf, np.ones(Bf.shape[2] * Cf.shape[2]), R)
+    return 1.0 / np.array([np.linalg.norm(op.col(j)) for j in range(op.K)])
+
+
+def kron_truncation_eps_gram(Bf, Cf, d, R_keep) -> np.ndarray:
+    """Exact eps_j = ||a~_j - a_j|| for the truncation to the first R_keep terms (closed form).
+
+    a_j - a~_j = d_j sum_{r >= R_keep} B_r[:, k1] (x) C_r[:, k2], and
+    ||sum_r b_r (x) c_r||^2 = sum_{r,s} (b_r . b_s)(c_r . c_s).
+    """
+    tb = Bf[R_keep:]
+    tc = Cf[R_keep:]
+    if tb.shape[0] == 0:
+        return np.zeros(Bf.shape[2] * Cf.shape[2])
+    GB = np.einsum("rnk,snk->rsk", tb, tb)
+    GC = np.einsum("rnk,snk->rsk", tc, tc)
+    sq = np.einsum("rsa,rsb->ab", GB, GC).reshape(-1)
+    return d * np.sqrt(np.maximum(sq, 0.0))
+
+
+# ----------------------------------------------------------------------------- quantisers
+
+def to_f32(a) -> np.ndarray:
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def bf16_round(a) -> np.ndarray:
+    """Round FP32 values to BF16 (8 exponent bits, 7 mantissa bits), round to nearest, ties to even.
+
+    BF16 is the top half of the FP32 encoding: add half an ulp of the kept part (plus the
+    kept part's last bit, which breaks ties towards even) and truncate the low 16 bits.
+    """
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    bits = f.view(np.uint32).astype(np.uint64)
+    rounded = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return rounded.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+E4M3_MAX = 448.0
+
+
+def e4m3_round(v) -> np.ndarray:
+    """Round FP32 values to FP8 E4M3 ('fn' variant: bias 7, no infinities), ties to even, saturating.
+
+    Normal numbers have a 3-bit mantissa, so the spacing at |v| in [2^e, 2^(e+1)) is 2^(e-3);
+    below 2^-6 the format is subnormal with fixed spacing 2^-9.  Magnitudes that round above
+    the largest finite value 448 saturate to 448.
+    """
+    v = np.asarray(v, dtype=np.float64)
+    a = np.abs(v)
+    _, ex = np.frexp(a)                 # a = m 2^ex, m in [0.5, 1)
+    e = np.maximum(ex - 1, -6)          # floor(log2 a), clamped to the subnormal exponent
+    quantum = np.ldexp(1.0, e - 3)
+    q = np.rint(a / quantum) * quantum  # np.rint rounds half to even
+    q = np.minimum(q, E4M3_MAX)
+    return np.sign(v) * q
+
+
+def fp8_atom_scale(A) -> np.ndarray:
+    """Per-atom scale s_j = fl32(max_i |a_ij| / 448) (FP64 quotient, then rounded to FP32)."""
+    m = np.max(np.abs(np.asarray(A, dtype=np.float64)), axis=0)
+    s = to_f32(m / E4M3_MAX)
+    return np.where(s > 0, s, 1.0)
+
+
+def fp8_quantize(A):
+    """Per-atom scaled E4M3 copy: q_ij = E4M3(fl32(a_ij / s_j)), a~_ij = s_j q_ij (exact in FP64)."""
+    A32 = np.asarray(A, dtype=np.float32)
+    s = fp8_atom_scale(A)
+    v = (A32 / s.astype(np.float32)[None, :]).astype(np.float64)   # IEEE FP32 division
+    q = e4m3_round(v)
+    return q * s[None, :], q, s
+
+
+# ----------------------------------------------------------------------------- ladder
+
+@dataclass
+class Level:
+    """One approximate dictionary A~^i with its error bounds and relative complexity."""
+    name: str
+    op: object                  # DenseDict or KronDict
+    eps: np.ndarray             # K, eps_j >= ||a~_j - a_j||_2
+    rc: float                   # relative complexity RC(A~^i) (eq:complexity_model_approx)
+    atnorm: np.ndarray          # K, ||a~_j||_2 (used by the look-ahead estimate K_t)
+
+
+def exact_errors(approx_cols: np.ndarray, exact_cols: np.ndarray) -> np.ndarray:
+    """eps_j = ||a~_j - a_j||_2 evaluated in FP64, inflated by EPS_SAFETY to stay an upper bound."""
+    diff = np.asarray(approx_cols, np.float64) - np.asarray(exact_cols, np.float64)
+    return np.sqrt(np.einsum("nk,nk->k", diff, diff)) * (1.0 + EPS_SAFETY)
+
+
+def dense_level(name, approx: np.ndarray, exact: np.ndarray, rc: float) -> Level:
+    op = DenseDict(approx)
+    return Level(name, op, exact_errors(approx, exact), rc, op.atom_norms())
+
+
+def exact_level(A: np.ndarray) -> Level:
+    op = DenseDict(A)
+    return Level("exact", op, np.zeros(op.K), 1.0, op.atom_norms())
+
+
+def kron_level(Bf, Cf, d, R_keep, exact_dense=None, rc=None) -> Level:
+    """Truncation A~^(R) = (sum_{r < R_keep} B_r (x) C_r) diag(d), d of the full sum.
+
+    eps_j is the closed form of ``kron_truncation_eps_gram`` when the exact dictionary is the
+    full Kronecker sum, or the explicit column differences when ``exact_dense`` is given.
+    RC defaults to the theoretical ratio R_keep (2 N1 K1 K2 + 2 N1 K2 N2) / (2 N K).
+    """
+    op = KronDict(Bf, Cf, d, R_keep)
+    if exact_dense is None:
+        eps = kron_truncation_eps_gram(Bf, Cf, d, R_keep) * (1.0 + EPS_SAFETY)
+    else:
+        eps = exact_errors(op.dense(), exact_dense)
+    if rc is None:
+        rc = R_keep * (op.N1 * op.K1 * op.K2 + op.N1 * op.K2 * op.N2) / (op.N * op.K)
+    atn = np.sqrt(np.maximum(
+        np.einsum("rsa,rsb->ab",
+                  np.einsum("rnk,snk->rsk", op.Bf[:R_keep], op.Bf[:R_keep]),
+                  np.einsum("rnk,snk->rsk", op.Cf[:R_keep], op.Cf[:R_keep])).reshape(-1), 0.0)) * d
+    return Level(f"kron{R_keep}", op, eps, rc, atn)
+
+
+def power_iteration_sq_norm(op, iters: int = 200, safety: float = 1.001) -> float:
+    """L = safety * ||A||_2^2 estimated by power iteration on A^T A from the all-ones vector."""
+    v = np.ones(op.K) / np.sqrt(op.K)
+    s = 0.0
+    for _ in range(iters):
+        w = op.rmatvec(op.matvec(v))
+        s = float(np.linalg.norm(w))
+        if s == 0.0:
+            return 0.0
+        v = w / s
+    return safety * s

@@ -1,0 +1,104 @@
+"""Pins of the oracle's dictionaries, quantisers and error bounds (no GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import dictionaries as D
+
+
+def _f32_samples(n, seed):
+    r = np.random.default_rng(seed)
+    v = (r.standard_normal(n) * np.exp2(r.integers(-12, 12, n))).astype(np.float32)
+    # exact ties of the BF16 rounding: 16 low bits = 0x8000
+    bits = v.view(np.uint32).copy()
+    bits[: n // 8] = (bits[: n // 8] & 0xFFFF0000) | 0x8000
+    return bits.view(np.float32)
+
+
+def test_bf16_matches_torch_cast():
+    v = _f32_samples(200000, 1)
+    ours = D.bf16_round(v)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(ours, ref)
+
+
+def test_e4m3_matches_torch_cast_in_range_and_saturates():
+    r = np.random.default_rng(2)
+    v = (r.standard_normal(200000) * np.exp2(r.integers(-11, 9, 200000))).astype(np.float32)
+    v = np.clip(v, -448, 448)
+    # exact midpoints between neighbouring E4M3 values, to pin ties-to-even
+    grid = torch.arange(0, 127, dtype=torch.uint8).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    mids = ((grid[1:] + grid[:-1]) / 2).astype(np.float32)
+    v = np.concatenate([v, mids, -mids])
+    ours = D.e4m3_round(v)
+    ref = torch.from_numpy(v).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(ours, ref)
+    big = np.array([449.0, 463.9, 464.0, 500.0, 1e6, -1e6], dtype=np.float32)
+    np.testing.assert_array_equal(D.e4m3_round(big), np.sign(big) * 448.0)
+
+
+def test_fp8_atom_scaled_copy():
+    A = S.dense_small(N=64, K=100, n_signals=1).A
+    At, q, s = D.fp8_quantize(A)
+    assert np.all(np.abs(q) <= 448.0)
+    np.testing.assert_array_equal(At, q * s[None, :])
+    # the largest entry of every atom lands near the top of the FP8 range
+    assert np.all(np.max(np.abs(q), axis=0) >= 416.0)
+    lev = D.dense_level("fp8", At, A, 0.25)
+    np.testing.assert_allclose(lev.eps, np.linalg.norm(At - A, axis=0), rtol=1e-11)
+    # E4M3 has a 3-bit mantissa: relative rounding error at most 2^-4 on normal values
+    assert np.all(lev.eps <= 2.0 ** -4 * np.linalg.norm(A, axis=0))
+
+
+def test_kron_operator_against_explicit_kron():
+    w = S.kron_small(R=3, N1=4, K1=6, N2=5, K2=7, n_signals=1)
+    d = D.kron_unit_scale(w.Bf, w.Cf)
+    M = sum(np.kron(w.Bf[r], w.Cf[r]) for r in range(3)) * d[None, :]
+    op = D.KronDict(w.Bf, w.Cf, d)
+    r = np.random.default_rng(3)
+    x, rho = r.standard_normal(op.K), r.standard_normal(op.N)
+    np.testing.assert_allclose(op.matvec(x), M @ x, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(op.rmatvec(rho), M.T @ rho, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(op.dense(), M, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(np.linalg.norm(M, axis=0), 1.0, rtol=1e-13)
+    idx = np.array([0, 5, 17, 40])
+    np.testing.assert_allclose(op.matvec(x[idx], idx), M[:, idx] @ x[idx], atol=1e-13)
+    np.testing.assert_allclose(op.rmatvec(rho, idx), M[:, idx].T @ rho, atol=1e-13)
+
+
+def test_kron_truncation_eps_gram_equals_column_differences():
+    w = S.kron_small(R=4, N1=5, K1=6, N2=4, K2=8, n_signals=1)
+    d = D.kron_unit_scale(w.Bf, w.Cf)
+    full = D.KronDict(w.Bf, w.Cf, d).dense()
+    for Rk in (1, 2, 3, 4):
+        trunc = D.KronDict(w.Bf, w.Cf, d, Rk).dense()
+        np.testing.assert_allclose(D.kron_truncation_eps_gram(w.Bf, w.Cf, d, Rk),
+                                   np.linalg.norm(trunc - full, axis=0), rtol=1e-10, atol=1e-14)
+        lev = D.kron_level(w.Bf, w.Cf, d, Rk)
+        np.testing.assert_allclose(lev.atnorm, np.linalg.norm(trunc, axis=0), rtol=1e-10)
+
+
+def test_generator_kron_norms_agree_with_oracle():
+    w = S.kron_small(R=3, N1=4, K1=6, N2=5, K2=7, n_signals=1)
+    np.testing.assert_allclose(1.0 / S.gen.kron_column_norms(w.Bf, w.Cf), D.kron_unit_scale(w.Bf, w.Cf),
+                               rtol=1e-12)
+
+
+def test_power_iteration_matches_spectral_norm():
+    A = S.dense_small(N=50, K=120, n_signals=1).A
+    L = D.power_iteration_sq_norm(D.DenseDict(A), iters=500, safety=1.0)
+    ref = np.linalg.norm(A, 2) ** 2
+    assert abs(L - ref) <= 1e-6 * ref
+    assert D.power_iteration_sq_norm(D.DenseDict(A), iters=500) >= ref
+
+
+@pytest.mark.parametrize("decay", [None, 0.5])
+def test_c2_levels_shapes_and_errors(decay):
+    """c2 dictionary: unit atoms; truncation errors decrease with R and vanish at R = 4."""
+    w = S.c2(decay=decay)
+    d = 1.0 / S.gen.kron_column_norms(w.Bf, w.Cf)
+    e = [D.kron_truncation_eps_gram(w.Bf, w.Cf, d, R) for R in (1, 2, 3, 4)]
+    assert all(np.all(a >= b - 1e-12) for a, b in zip(e, e[1:]))
+    assert np.max(e[-1]) == 0.0
+    assert w.N == 1024 and w.K == 4096
