@@ -1,0 +1,360 @@
+"""Throughput of the screened mixed-precision Lasso solve on one GB300 (or N, weak scaling).
+
+Workload (one step): the batched mixed-precision configuration -- a dense 2048 x 8192 FP32
+dictionary with unit atoms, 4096 signals y_i = A x0_i with Bernoulli(p_i) x0, p_i ~ U[0.01, 0.05],
+lambda_i / lambda_max,i ~ U[0.1, 0.9], solved to relative duality gap 1e-6 over the ladder
+FP8 (per-atom scaled E4M3) -> BF16 -> FP32 (exact), every signal certified by the full-dictionary
+gap.  A solve counts when its certified gap is <= tol.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--signals B]
+N > 1 runs under torchrun, one rank per GPU, each rank solving its own 4096 signals.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Lasso solves/sec at rel. gap 1e-6: screened mixed-prec vs plain FISTA, GB/s"
+UNIT = "solves/s"
+TOL = 1e-6
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--signals", type=int, default=4096)
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def _workload_config(B):
+    return {"workload": f"c3 batched mixed precision: dense 2048x8192 FP32 dictionary (unit atoms), {B} signals "
+                        "per GPU, x0 Bernoulli(p_i) p_i~U[0.01,0.05], lambda_i/lambda_max~U[0.1,0.9], rel gap 1e-6",
+            "N": 2048, "K": 8192, "signals_per_gpu": B, "ladder": ["fp8_e4m3_atom_scaled", "bf16", "f32_exact"],
+            "tol": TOL, "certify_full": True, "l2": "flushed between timed steps (512 MB write)"}
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+
+def _oracle_rate(w, seconds, max_signals=64):
+    """Oracle (FP64 numpy Algorithm 1, same ladder) on the first signals until `seconds` pass."""
+    from oracle import dictionaries as OD
+    from oracle import lasso as OL
+    from oracle import solvers as OS
+    A = w.A
+    f8, _, _ = OD.fp8_quantize(A)
+    levels = [OD.dense_level("fp8", f8, A, 0.25), OD.dense_level("bf16", OD.bf16_round(A), A, 0.5),
+              OD.exact_level(A)]
+    Lip = OD.power_iteration_sq_norm(levels[-1].op, iters=50) * 1.01
+    t0 = time.perf_counter()
+    n = 0
+    while n < min(max_signals, w.Y.shape[0]) and time.perf_counter() - t0 < seconds:
+        y = w.Y[n]
+        Aty = A.T @ y
+        lam = w.lam_ratio[n] * OL.lambda_max(Aty)
+        r = OS.fast_l1(levels, levels[-1].atnorm, y, lam, TOL, Gamma=0.5, Lip=Lip, Aty=Aty)
+        n += int(r.converged)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import synthetic as S
+    w = S.c3(n_signals=64)
+    times, solved = [], 0
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm state; warm-up steps are empty
+    per_step = max(5.0, min(60.0, 150.0 / max(1, args.steps)))
+    for _ in range(args.steps):
+        rate, n, dt = _oracle_rate(w, per_step)
+        times.append(dt)
+        solved += n
+    tot = sum(times)
+    value = solved / tot if tot > 0 else 0.0
+    sample = f"first signals of the c3 batch, about {per_step:.0f} s of oracle work per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _workload_config(4096),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- comparator
+
+def plain_fista(A_t, Y, lam, L, tol, max_iter=3000, check_every=10):
+    """Plain FP32 FISTA without screening (torch FP32 GEMMs, TF32 off), gap checked every
+    `check_every` passes with FP64 scalars; returns (#signals below tol, seconds, passes)."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    B, N = Y.shape
+    K = A_t.shape[0]
+    X = torch.zeros((B, K), device=Y.device)
+    Zc = torch.zeros_like(X)
+    t = 1.0
+    yy = (Y.double() ** 2).sum(1)
+    lam_c = lam.float()[:, None]
+    done = torch.zeros(B, dtype=torch.bool, device=Y.device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it = 0
+    for it in range(1, max_iter + 1):
+        R = Y - Zc @ A_t                      # B x N
+        G = R @ A_t.T                         # B x K
+        if it % check_every == 0:
+            rr = (R.double() ** 2).sum(1)
+            yr = (Y.double() * R.double()).sum(1)
+            m = G.abs().max(1).values.double()
+            beta = yr / (lam * rr)
+            s = torch.clamp(beta, -1.0 / m, 1.0 / m)
+            P = 0.5 * rr + lam * Zc.double().abs().sum(1)
+            D = lam * s * yr - 0.5 * lam * lam * s * s * rr
+            done |= (P - D) / yy <= tol
+            if bool(done.all()):
+                break
+        Xn = Zc + G / L
+        Xn = torch.sign(Xn) * torch.clamp(Xn.abs() - lam_c / L, min=0.0)
+        tn = 0.5 * (1.0 + (1.0 + 4.0 * t * t) ** 0.5)
+        Zc = Xn + ((t - 1.0) / tn) * (Xn - X)
+        X, t = Xn, tn
+    torch.cuda.synchronize()
+    return int(done.sum()), time.perf_counter() - t0, it
+
+
+def _traffic(kind):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if the
+    kernel source has not changed since (hash recorded with the counters)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p)).get(kind)
+        src = open(os.path.join(ROOT, d["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != d["sha256_16"]:
+            return None
+        return d["dram_bytes_per_launch"]
+    except (KeyError, OSError, TypeError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import synthetic as S
+    import paper_1812_06635_gb300 as pkg
+    from paper_1812_06635_gb300 import build
+    build.build()
+    pkg.load()
+
+    B = args.signals
+    w = S.c3(n_signals=B, first=rank * B)
+    d = pkg.Dictionary.dense(w.A, dtype="f32").add_level(pkg.LEVEL_FP8).add_level(pkg.LEVEL_BF16).prepare()
+    Y = torch.tensor(w.Y, dtype=torch.float32, device=dev)
+    ratios = torch.tensor(w.lam_ratio, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(profile=0):
+        return d.solve_batch(Y, ratios, TOL, stream=stream, lambda_relative=1, profile=profile)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    total_ms, solved, kms, kbytes, klaunch, launches = 0.0, 0, np.zeros(6), np.zeros(6), np.zeros(6), 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        X, gaps, status, iters, st = step(profile=1)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        solved += int(((status == 0) & (gaps <= TOL)).sum())
+        kms += np.array(st.kernel_ms)
+        kbytes += np.array(st.kernel_bytes)
+        klaunch += np.array(st.kernel_launches)
+        launches += st.launches
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t_local = total_ms / 1e3
+    if world > 1:
+        tt = torch.tensor([t_local, float(solved)], dtype=torch.float64, device=dev)
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t_job, solved_job = float(tmax[0]), int(tt[1])
+    else:
+        t_job, solved_job = t_local, solved
+    value = solved_job / t_job
+
+    # e2e: the same solve through the C ABI with pinned host buffers, copies included
+    Yh = torch.empty(Y.shape, dtype=torch.float32, pin_memory=True)
+    Yh.copy_(Y)
+    lh = torch.empty(B, dtype=torch.float64, pin_memory=True)
+    lh.copy_(ratios)
+    Xh = torch.empty((B, w.K), dtype=torch.float32, pin_memory=True).numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xo, go, so, st_e2e = d.solve_batch_host(Yh.numpy(), lh.numpy(), TOL, lambda_relative=1)
+    e2e_s = time.perf_counter() - t0
+    e2e_solved = int(((so == 0) & (go <= TOL)).sum())
+    del Xh
+
+    # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
+    hbm, bf16, peak_src = _peaks()
+    kind = int(np.argmax(kms))
+    names = ["k_residual", "k_corr", "k_screen", "k_schedule", "k_kron_gemm", "k_tc_gemm"]
+    achieved = kbytes[kind] / (kms[kind] * 1e-3) / 1e9 if kms[kind] > 0 else 0.0
+    per_launch_bytes = kbytes[kind] / max(1.0, klaunch[kind])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": _traffic(names[kind]), "kernel": names[kind],
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "avg_launch_us": 1e3 * kms[kind] / max(1.0, klaunch[kind]),
+                "kernel_share": {names[i]: kms[i] / max(1e-9, kms.sum()) for i in range(6) if kms[i] > 0}}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            rate, n, dt = _oracle_rate(S.c3(n_signals=64), args.cpu_seconds)
+            cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"{n} signals of c3 solved by the FP64 numpy oracle (same ladder) in {dt:.1f} s "
+                             "(numpy BLAS threads on all host cores)"}
+        comp = None
+        if not args.no_comparator:
+            A_t = torch.tensor(w.A.T, dtype=torch.float32, device=dev).contiguous()   # K x N
+            lam = ratios * d.lambda_max(Y)
+            info = d.info()
+            nsolved, secs, its = plain_fista(A_t, Y, lam, info["L"], TOL)
+            comp = {"impl": "plain FP32 unscreened FISTA (torch FP32 GEMM, TF32 off, gap every 10 passes)",
+                    "value": nsolved / secs, "unit": UNIT, "solved": nsolved, "signals": B, "seconds": secs,
+                    "passes": its}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": _workload_config(B),
+                "solved_per_step": solved / args.steps, "signals_per_step": B * world,
+                "e2e": {"value": e2e_solved / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(B * w.N * 4 + B * 8),
+                        "d2h_bytes_per_step": int(B * w.K * 4 + B * 8 + B * 4)},
+                "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "comparator": comp,
+                "clocks": clk, "passes_max": st.passes,
+                "level_passes_per_signal": [v / B for v in st.level_passes[:3]],
+                "level_atom_passes_per_signal": [v / B for v in st.level_atoms[:3]]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    d.close()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * lasso.h -- C ABI of the GB300 screened Lasso solver.
+ *
+ * The library solves   x* = argmin_x 1/2 ||A x - y||_2^2 + lambda ||x||_1          (eq:lasso)
+ * with FISTA (or ISTA) restricted to the atoms that survive dynamic safe screening, while
+ * iterating on a ladder of approximate dictionaries A~^0, ..., A~^I = A of increasing
+ * precision (Algorithm 1, FastL1).  Screening uses the stable GAP Safe sphere of Theorem 1
+ * (or the stable Dynamic Safe sphere of Table I) with per-atom error bounds
+ * eps_j >= ||a~_j - a_j||_2, so every rejection is safe for the original problem; the
+ * dictionary switches on gap saturation or on the speed criterion (Algorithm 2).
+ *
+ * Conventions
+ *  - A dictionary has N rows (signal dimension) and K atoms (columns).  Dense inputs may be
+ *    given atom-major (row j = atom j, length N, leading dimension ld >= N) or column-major
+ *    (the usual N x K "columns are atoms" layout with leading dimension ld >= N, i.e. the
+ *    same memory); both mean element (n, j) at A[j * ld + n].  Row-major N x K input is
+ *    given with atom_major = 0 and ld >= K: element (n, j) at A[n * ld + j].
+ *  - Kronecker dictionaries: A = (sum_{r<R} B_r (x) C_r) diag(d) with B_r: N1 x K1 and
+ *    C_r: N2 x K2 row-major, N = N1 N2, K = K1 K2, atom k1 K2 + k2, row n1 N2 + n2, and
+ *    d_j = 1 / ||(sum_r B_r (x) C_r) e_j||_2 computed by the library in FP64 (unit atoms).
+ *  - "Relative gap" is G / ||y||^2 where G is an upper bound of the duality gap of the
+ *    returned point for the original problem (rounding of every kernel is folded in).
+ *  - Every call returns a status (lasso_status) and never aborts; on error the outputs are
+ *    left as documented per call.  lasso_strerror() gives a message.
+ *  - Pointers named *_host are host memory; pointers named d_* are device memory of the
+ *    current CUDA device.  The library owns every lasso_dict it creates.
+ *  - Thread safety: a lasso_dict may be used by one call at a time.
+ */
+#ifndef LASSO_GB300_H
+#define LASSO_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LASSO_OK = 0,
+    LASSO_ERR_INVALID_ARG = -1,   /* bad size, null pointer, wrong order of calls         */
+    LASSO_ERR_CUDA = -2,          /* a CUDA runtime call failed                           */
+    LASSO_ERR_NONFINITE = -3,     /* NaN/Inf met in the data or in a gap                  */
+    LASSO_ERR_MAXITER = -4,       /* max_iter passes without reaching tol (x is partial)  */
+    LASSO_ERR_TIMEOUT = -5,       /* wall-clock budget exceeded (x is partial)            */
+    LASSO_ERR_UNSUPPORTED = -6,   /* valid request this build does not handle             */
+    LASSO_ERR_NOMEM = -7,         /* device allocation failed                             */
+    LASSO_WARN_AUDIT = 1          /* full-dictionary certificate above tol (see gap)      */
+} lasso_status;
+
+typedef enum { LASSO_F64 = 0, LASSO_F32 = 1 } lasso_dtype;
+
+/* Approximate-dictionary kinds for lasso_dict_add_level (Section III-A, "precision" levels). */
+typedef enum {
+    LASSO_LEVEL_BF16 = 2,         /* BF16 copy of A (round to nearest even)                    */
+    LASSO_LEVEL_FP8 = 3,          /* E4M3 copy with per-atom scale s_j = max_i |a_ij| / 448     */
+    LASSO_LEVEL_KRON = 4,         /* Kronecker truncation to the first `param` terms            */
+    LASSO_LEVEL_F32 = 5           /* FP32 copy of an FP64 dictionary                            */
+} lasso_level_kind;
+
+typedef struct lasso_dict lasso_dict;
+
+/* Create a dense dictionary (the exact A of the problem).  dt gives the element type of A and
+ * the precision of the exact level (FP64 data: FP64 arithmetic; FP32 data: FP32 products with
+ * compensated accumulation).  normalize != 0 rescales every atom to unit l2 norm first (in
+ * FP64, then rounded to dt); the problem solved is then the one with normalised atoms.
+ * host_ptr != 0 if A is host memory.  The library copies A.  *out is NULL on error. */
+int lasso_dict_create_dense(const void* A, lasso_dtype dt, int64_t N, int64_t K, int64_t ld,
+                            int atom_major, int normalize, int host_ptr, lasso_dict** out);
+
+/* Create a sum-of-Kronecker dictionary (SuKro, Section V-A) from its factors (FP32, host or
+ * device).  The exact A is the FP64 Kronecker sum with unit atoms; the library stores a dense
+ * FP32 rounding of it as the last level (its rounding error enters eps_j), and the structured
+ * truncations are added with lasso_dict_add_level(LASSO_LEVEL_KRON, R'). */
+int lasso_dict_create_kron(const float* B, const float* C, int R, int N1, int K1, int N2, int K2,
+                           int host_ptr, lasso_dict** out);
+
+/* Append an approximate dictionary below the exact one.  Levels must be added from the
+ * coarsest to the finest; the exact dictionary always stays last (A~^I = A).  eps_j is
+ * computed exactly in FP64 against the exact atoms.  param: number of Kronecker terms for
+ * LASSO_LEVEL_KRON, ignored otherwise.  Up to 7 approximate levels. */
+int lasso_dict_add_level(lasso_dict* dict, lasso_level_kind kind, int param);
+
+/* Set the relative complexity RC of level `level` (eq:complexity_model_approx) used by the
+ * speed criterion of Algorithm 2; by default RC is the level's bytes (dense) or FLOPs
+ * (Kronecker) per full product over those of the exact dense product. */
+int lasso_dict_set_rc(lasso_dict* dict, int level, double rc);
+
+/* Step size: L = 1.001 max_i ||A~^i||_2^2 by 200 power iterations on the device, unless
+ * L_override > 0 is given.  Called automatically by the first solve when not called. */
+int lasso_dict_prepare(lasso_dict* dict, double L_override);
+
+typedef struct {
+    int64_t N, K;
+    int n_levels;                 /* including the exact level (last)                   */
+    double L;                     /* step constant (0 before prepare)                   */
+    int kind[8];                  /* lasso_level_kind of each level; exact: -1 (F64) / -2 (F32) */
+    double rc[8];
+    double eps_mean[8], eps_max[8];
+} lasso_dict_info_t;
+
+int lasso_dict_info(const lasso_dict* dict, lasso_dict_info_t* info);
+
+/* Copy level data back for inspection (tests): eps (K doubles) and, for dense levels, the
+ * dequantised atoms as FP64 (K x N atom-major, row j = a~_j).  Either output may be NULL. */
+int lasso_dict_level_host(const lasso_dict* dict, int level, double* eps_host, double* atoms_host);
+
+void lasso_dict_destroy(lasso_dict* dict);
+
+typedef enum { LASSO_FISTA = 0, LASSO_ISTA = 1 } lasso_algo;
+typedef enum { LASSO_RULE_GAP = 0, LASSO_RULE_DST = 1 } lasso_rule;
+
+typedef struct {
+    double Gamma;            /* switching threshold of Algorithm 2 (default 0.5)                */
+    int algo;                /* lasso_algo (default FISTA)                                      */
+    int rule;                /* lasso_rule (default stable GAP Safe)                            */
+    int screen_every;        /* screen every k passes (default 1)                               */
+    int max_iter;            /* per-signal pass limit (default 100000)                          */
+    int lambda_relative;     /* 1: lambdas are lambda / lambda_max of each signal (default 0)   */
+    int final_fp64;          /* 1: append an FP64-accumulation rung on the exact data and keep
+                                FP64 iterates (tight tolerances; default 0)                     */
+    int certify_full;        /* 1: final full-dictionary pass for the reported gap (default 1)  */
+    int passes_per_sync;     /* passes per captured CUDA graph replay (default 8)               */
+    int tensor_cores;        /* 1: batched BF16/FP8 levels use the tcgen05 GEMMs (default 1)   */
+    double tau;              /* rejection guard: reject iff test < 1 - tau (default 1e-9)       */
+    double time_limit_s;     /* 0: none                                                          */
+    int profile;             /* 1: time every kernel of the passes with CUDA events (stats)     */
+} lasso_opts;
+
+/* Fill *opts with the defaults above. */
+void lasso_opts_default(lasso_opts* opts);
+
+typedef struct {
+    int64_t passes;          /* passes executed (max over signals for a batch)                  */
+    int64_t level_passes[8]; /* passes spent on each level, summed over signals                 */
+    int64_t kept_final;      /* |A| at exit (single solve) or its sum over the batch            */
+    double lambda_max;       /* lambda_max of the (first) signal                                */
+    double lambda;           /* lambda used for the (first) signal                              */
+    double seconds;          /* wall time of the call                                           */
+    int64_t launches;        /* kernels launched by the call (all kinds)                        */
+    /* per kernel kind (0 residual, 1 correlation + update, 2 screening, 3 schedule,
+       4 Kronecker GEMMs, 5 tensor-core GEMMs): launches, device milliseconds (with
+       opts.profile) and algorithmic bytes (dictionary rows, signals and iterates read or
+       written by the definition of the step) */
+    int64_t kernel_launches[6];
+    double kernel_ms[6];
+    double kernel_bytes[6];
+    double level_atoms[8];   /* sum over passes and signals of |A_t| on each level              */
+} lasso_stats;
+
+/* Solve one signal (host buffers).  y: N values (rounded to the exact level's precision on
+ * entry).  lambda: absolute, or relative to lambda_max if opts->lambda_relative.  Outputs:
+ * x_host (K, zero outside the preserved set), gap_host (relative gap of the returned point),
+ * kept_host (capacity K, sorted preserved set at exit, may be NULL), n_kept (may be NULL),
+ * stats (may be NULL).  lambda >= lambda_max returns x = 0, gap = 0, n_kept = 0. */
+int lasso_solve(lasso_dict* dict, const double* y_host, double lambda, double tol,
+                const lasso_opts* opts, double* x_host, double* gap_host, int32_t* kept_host,
+                int64_t* n_kept, lasso_stats* stats);
+
+/* Solve B signals in one batch on `stream` (a cudaStream_t, NULL = default stream).  Device
+ * buffers: d_Y (B x N FP32, row b = y_b), d_lambdas (B FP64), d_X (B x K FP32 output),
+ * d_gaps (B FP64 output), d_status (B int32 output: lasso_status per signal), d_iters (B int32
+ * output, may be NULL).  Synchronises the stream before returning. */
+int lasso_solve_batch(lasso_dict* dict, const float* d_Y, const double* d_lambdas, int64_t B,
+                      double tol, const lasso_opts* opts, float* d_X, double* d_gaps,
+                      int32_t* d_status, int32_t* d_iters, void* stream, lasso_stats* stats);
+
+/* Same with host buffers: copies inputs to the device, solves, copies results back. */
+int lasso_solve_batch_host(lasso_dict* dict, const float* Y_host, const double* lambdas_host,
+                           int64_t B, double tol, const lasso_opts* opts, float* X_host,
+                           double* gaps_host, int32_t* status_host, lasso_stats* stats);
+
+/* lambda_max = ||A^T y||_inf of B signals (device buffers, exact level, FP64 output). */
+int lasso_lambda_max(lasso_dict* dict, const float* d_Y, int64_t B, double* d_out, void* stream);
+
+/* Derivative of L(x*(y, A)) through the support system (not in the paper; derived from the
+ * KKT conditions of Section II): with S = supp(x_b), u = (A_S^T A_S)^{-1} g_S,
+ * dL/dy_b = A_S u and dL/dA[:, S] += r u^T - (A_S u) x_S^T, r = y_b - A_S x_S.  lambda is held
+ * fixed.  Device buffers: d_Y (B x N), d_X (B x K solution), d_G (B x K, dL/dx), outputs
+ * d_dY (B x N) and d_dA (K x N atom-major, accumulated over the batch; may be NULL).  Uses
+ * the exact level of a dense dictionary; supports up to 1024 nonzeros per signal. */
+int lasso_backward(lasso_dict* dict, const float* d_Y, const float* d_X, const float* d_G,
+                   int64_t B, float* d_dY, float* d_dA, void* stream);
+
+const char* lasso_strerror(int status);
+
+/* Build information ("sm_103a ..."). */
+const char* lasso_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LASSO_GB300_H */

@@ -1,0 +1,187 @@
+// Shared device types and helpers of the GB300 screened Lasso library.
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <cmath>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "../../include/lasso.h"
+
+namespace lasso {
+
+constexpr int MAX_LEVELS = 8;
+constexpr int VEC_BYTES = 16;        // every dense row is padded to a multiple of 16 elements
+constexpr int CORR_CHUNK = 32;       // atoms of the preserved list per correlation work item
+constexpr int RES_THREADS = 256;
+
+// Arithmetic kind of a level.
+enum LevelKind : int {
+  LK_F64 = 0,     // FP64 data, FP64 accumulation
+  LK_F32 = 1,     // FP32 data, error-free FP32 products and compensated accumulation (Dot2)
+  LK_BF16 = 2,    // BF16 data, FP32 products, compensated accumulation
+  LK_FP8 = 3,     // E4M3 data with per-atom FP32 scale, FP32 products
+  LK_KRON = 4,    // sum of Kronecker products, FP32 small GEMMs
+  LK_F32D = 5     // FP32 data, FP64 accumulation (final FP64 rung of an FP32 dictionary)
+};
+
+__host__ __device__ inline bool level_is_dense(int k) { return k != LK_KRON; }
+enum ResModel : int { RES_FOLD = 0, RES_CHAIN = 1, RES_DOT2 = 2 };
+__host__ __device__ inline bool level_fp64_arith(int k) { return k == LK_F64 || k == LK_F32D; }
+
+// One rung of the ladder, as the kernels see it.
+struct LevelDev {
+  int kind;
+  int64_t ld;               // dense: elements per atom row (multiple of 16)
+  const void* data;         // dense: K x ld atom-major
+  const float* scale;       // FP8: per-atom scale
+  const double* eps;        // eps_j >= ||a~_j - a_j|| (dictionary error only)
+  const double* kappa;      // kappa_j: bound of sum_i |a~_ij| |v_i| / ||v|| (||a~_j|| or Kronecker form)
+  const float* atnorm;      // ||a~_j||
+  // Rounding of the correlation: |g^_j - a~_j^T rho^| <= gam_corr kappa_j ||rho^|| + 3 u_g |g^_j|,
+  // so the stable test and the dual scaling use eps_j + gam_corr kappa_j in place of eps_j.
+  double gam_corr;
+  // Rounding of the residual, e_r >= ||rho^ - (y - A~ z)||:
+  //   RES_FOLD:  gam_res sum_j |z_j| kappa_j + 2 u ||rho^||
+  //   RES_CHAIN: gamma_{nnz+4}(u64) sum_j |z_j| kappa_j + 2 u ||rho^||
+  //   RES_DOT2:  (2 gamma_{2 nnz + 2}(u32)^2 + gam_res) sum_j |z_j| kappa_j + 2 u ||rho^||
+  int res_model;
+  double gam_res;
+  double rc;                // relative complexity (Algorithm 2)
+  // Kronecker factors (LK_KRON): A~ = (sum_{r<R} B_r (x) C_r) diag(d)
+  const float* B;
+  const float* C;
+  const float* dscale;      // d_j as FP32 (the FP64 value enters through kappa / eps)
+  int R, N1, K1, N2, K2;
+};
+
+struct DictDev {
+  int N, K, n_levels;
+  int64_t ldN;              // padded signal length (multiple of 16)
+  const double* anorm;      // exact ||a_j||_2, rounded up
+  LevelDev lv[MAX_LEVELS];
+};
+
+// Per-signal solver state (device memory, one per signal).
+struct SigState {
+  double lam, yy, ynorm, t, beta;
+  double l1, sum_epsz, sum_kapz;     // of the current point z_t (its nonzero list)
+  double gap, Gp, Gt, gamma, Rp, delta, sp;
+  double lam_max_lb, lam_max_ub;
+  int level, n_kept, parity, n_nz, status, done, iters, Kt, n_chunks, pad0;
+  int level_passes[MAX_LEVELS];
+};
+
+// e_r >= ||rho^ - (y - A~ z)|| for the residual of the current pass (see LevelDev).
+__device__ __forceinline__ double residual_bound(const LevelDev& L, double sum_kapz, int n_nz, double nrho,
+                                                 bool vt64);
+
+// Knobs of a solve, as kernels see them.
+struct SolveParams {
+  double tol, Gamma, tau, L;
+  int algo, rule, screen_every, max_iter;
+  int B;
+};
+
+// ------------------------------------------------------------------ error-free transforms
+// TwoSum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Double-float accumulator (s, c): value s + c.
+struct DF {
+  float s, c;
+  __device__ __forceinline__ void init() { s = 0.f; c = 0.f; }
+  __device__ __forceinline__ void add(float p) {
+    float t, e;
+    two_sum(s, p, t, e);
+    s = t;
+    c = __fadd_rn(c, e);
+  }
+  __device__ __forceinline__ void merge(const DF& o) {
+    float t, e;
+    two_sum(s, o.s, t, e);
+    s = t;
+    c = __fadd_rn(__fadd_rn(c, o.c), e);
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Dot2 step (Ogita, Rump & Oishi, "Accurate sum and dot product", 2005): the product is split
+// exactly as p + q (FMA), p enters the running sum through TwoSum and the errors gather in c.
+__device__ __forceinline__ void dot2_add(DF& acc, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float q = __fmaf_rn(a, b, -p);
+  float t, e;
+  two_sum(acc.s, p, t, e);
+  acc.s = t;
+  acc.c = __fadd_rn(acc.c, __fadd_rn(e, q));
+}
+
+__device__ __forceinline__ DF df_shfl_xor(const DF& v, int m) {
+  DF o;
+  o.s = __shfl_xor_sync(0xffffffffu, v.s, m);
+  o.c = __shfl_xor_sync(0xffffffffu, v.c, m);
+  return o;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+constexpr double U32 = 5.9604644775390625e-08;    // 2^-24
+constexpr double U64 = 1.1102230246251565e-16;    // 2^-53
+
+// gamma_n = n u / (1 - n u) (Higham): bound of the relative error of an n-term recursive sum.
+__host__ __device__ inline double gamma_n(double n, double u) { return n * u / (1.0 - n * u); }
+
+
+// ------------------------------------------------------------------ host error helpers
+#define LASSO_CUDA_TRY(expr)                                                          \
+  do {                                                                                \
+    cudaError_t _e = (expr);                                                          \
+    if (_e != cudaSuccess) {                                                          \
+      lasso::set_last_error(cudaGetErrorString(_e), __FILE__, __LINE__);              \
+      return _e == cudaErrorMemoryAllocation ? LASSO_ERR_NOMEM : LASSO_ERR_CUDA;      \
+    }                                                                                 \
+  } while (0)
+
+void set_last_error(const char* msg, const char* file, int line);
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace lasso
+
+namespace lasso {
+__device__ __forceinline__ double residual_bound(const LevelDev& L, double sum_kapz, int n_nz, double nrho,
+                                                 bool vt64) {
+  const double urho = vt64 ? U64 : U32;
+  switch (L.res_model) {
+    case RES_CHAIN:
+      return gamma_n((double)n_nz + 4.0, U64) * sum_kapz + 2.0 * urho * nrho;
+    case RES_DOT2: {
+      const double g = gamma_n(2.0 * n_nz + 2.0, U32);
+      return (2.0 * g * g + L.gam_res) * sum_kapz + 2.0 * urho * nrho;
+    }
+    default:
+      return L.gam_res * sum_kapz + 2.0 * urho * nrho;
+  }
+}
+}  // namespace lasso

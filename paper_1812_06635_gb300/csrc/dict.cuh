@@ -1,0 +1,59 @@
+// Host-side dictionary object shared by the library's translation units.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace lasso {
+
+struct Workspace;   // solver buffers, defined in solver.cu
+
+struct HostLevel {
+  int kind = -1;               // LevelKind
+  int api_kind = 0;            // lasso_level_kind, or -1 (exact FP64) / -2 (exact FP32)
+  int param = 0;               // Kronecker terms
+  void* data = nullptr;        // dense payload (K x ldN)
+  float* scale = nullptr;      // FP8 scales
+  double* eps = nullptr;
+  double* kappa = nullptr;
+  float* atnorm = nullptr;
+  float* dscale = nullptr;     // Kronecker d_j as FP32
+  double u = U32, gam_corr = 0.0, gam_res = 0.0, rc = 1.0;
+  bool rc_set = false;
+  double eps_mean = 0.0, eps_max = 0.0;
+  bool owns_data = true;
+};
+
+}  // namespace lasso
+
+struct lasso_dict {
+  int device = 0;
+  int64_t N = 0, K = 0, ldN = 0;
+  int exact_kind = lasso::LK_F32;      // LK_F64 or LK_F32
+  bool is_kron = false;
+  int R = 0, N1 = 0, K1 = 0, N2 = 0, K2 = 0;
+  float* Bf = nullptr;                 // R x N1 x K1
+  float* Cf = nullptr;                 // R x N2 x K2
+  double* d = nullptr;                 // K, FP64 column scale
+  double* gramB = nullptr;             // R x R x K1
+  double* gramC = nullptr;             // R x R x K2
+  double* anorm = nullptr;             // K, exact atom norms (rounded up)
+  std::vector<lasso::HostLevel> approx;
+  lasso::HostLevel exact;
+  lasso::HostLevel rung64;             // FP64-accumulation rung on FP32 exact data (lazy)
+  double L = 0.0;
+  bool prepared = false;
+  lasso::Workspace* ws = nullptr;
+};
+
+namespace lasso {
+
+// Level descriptor for kernels.  vt_double: the solve iterates in FP64 (affects the roundings).
+LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double = false);
+// All levels of a solve, coarsest first, exact (or the FP64 rung) last.
+int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order);
+int ensure_rung64(lasso_dict* d);
+int dict_prepare(lasso_dict* d, double L_override);
+
+}  // namespace lasso

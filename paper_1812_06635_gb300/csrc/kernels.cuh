@@ -1,0 +1,166 @@
+// Device building blocks of one FISTA pass over the preserved atoms: atom-row dot products
+// with compensated accumulation, and the sparse residual accumulation.
+//
+// Rounding model (folded into the stable test by the callers, see LevelDev):
+//  * the exact FP32 level uses Dot2 (error-free products, TwoSum accumulation): the error of
+//    the unrounded result is second order, <= 2 gamma_{2n}^2 sum_i |a_i rho^_i|;
+//  * BF16 / FP8 levels: 2 products (the first rounded, the second fused) are summed in FP32
+//    and the pair is added exactly (TwoSum) into a double-float accumulator, so
+//    |g^ - a~^T rho^| <= gamma_3 sum_i |a~_i rho^_i|;
+//  * FP64-arithmetic levels: plain FP64 FMA chains.
+#pragma once
+
+#include "common.cuh"
+
+namespace lasso {
+
+__device__ __forceinline__ float2 bf16x2_to_f2(uint32_t v) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
+  return __bfloat1622float2(h);
+}
+
+__device__ __forceinline__ float2 fp8x2_to_f2(uint16_t v) {
+  __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)v, __NV_E4M3);
+  return __half22float2(*reinterpret_cast<__half2*>(&hr));
+}
+
+// Add the pair a0 r0 + a1 r1 (first product rounded, second fused) to the accumulator.
+__device__ __forceinline__ void df_pair(DF& acc, float a0, float r0, float a1, float r1) {
+  float p = __fmul_rn(a0, r0);
+  p = __fmaf_rn(a1, r1, p);
+  acc.add(p);
+}
+
+__device__ __forceinline__ DF df_warp_reduce(DF acc) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) acc.merge(df_shfl_xor(acc, m));
+  return acc;
+}
+
+// Warp dot product of atom row j of level L with the staged vector rho (shared memory).
+// rho_f: FP32 staging (float levels); rho_d: FP64 staging (FP64-arithmetic levels).
+// Returns the same value in every lane.
+__device__ __forceinline__ double warp_atom_dot(const LevelDev& L, int64_t j, int ldN, const float* __restrict__ rho_f,
+                                                const double* __restrict__ rho_d, int lane) {
+  switch (L.kind) {
+    case LK_F32: {
+      const float4* row = reinterpret_cast<const float4*>((const float*)L.data + j * L.ld);
+      const float4* rs = reinterpret_cast<const float4*>(rho_f);
+      DF acc;
+      acc.init();
+      const int nv = ldN >> 2;
+#pragma unroll 4
+      for (int k = lane; k < nv; k += 32) {
+        float4 a = __ldg(row + k);
+        float4 r = rs[k];
+        dot2_add(acc, a.x, r.x);
+        dot2_add(acc, a.y, r.y);
+        dot2_add(acc, a.z, r.z);
+        dot2_add(acc, a.w, r.w);
+      }
+      return df_warp_reduce(acc).value();
+    }
+    case LK_BF16: {
+      const uint4* row = reinterpret_cast<const uint4*>((const __nv_bfloat16*)L.data + j * L.ld);
+      const float4* rs = reinterpret_cast<const float4*>(rho_f);
+      DF acc;
+      acc.init();
+      const int nv = ldN >> 3;
+#pragma unroll 2
+      for (int k = lane; k < nv; k += 32) {
+        uint4 a = __ldg(row + k);
+        float4 r0 = rs[2 * k], r1 = rs[2 * k + 1];
+        float2 a0 = bf16x2_to_f2(a.x), a1 = bf16x2_to_f2(a.y), a2 = bf16x2_to_f2(a.z), a3 = bf16x2_to_f2(a.w);
+        df_pair(acc, a0.x, r0.x, a0.y, r0.y);
+        df_pair(acc, a1.x, r0.z, a1.y, r0.w);
+        df_pair(acc, a2.x, r1.x, a2.y, r1.y);
+        df_pair(acc, a3.x, r1.z, a3.y, r1.w);
+      }
+      return df_warp_reduce(acc).value();
+    }
+    case LK_FP8: {
+      const uint4* row = reinterpret_cast<const uint4*>((const uint8_t*)L.data + j * L.ld);
+      const float4* rs = reinterpret_cast<const float4*>(rho_f);
+      DF acc;
+      acc.init();
+      const int nv = ldN >> 4;
+      for (int k = lane; k < nv; k += 32) {
+        uint4 a = __ldg(row + k);
+        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float4 r = rs[4 * k + q];
+          float2 lo = fp8x2_to_f2((uint16_t)(w[q] & 0xffffu));
+          float2 hi = fp8x2_to_f2((uint16_t)(w[q] >> 16));
+          df_pair(acc, lo.x, r.x, lo.y, r.y);
+          df_pair(acc, hi.x, r.z, hi.y, r.w);
+        }
+      }
+      return df_warp_reduce(acc).value() * (double)L.scale[j];
+    }
+    case LK_F64: {
+      const double2* row = reinterpret_cast<const double2*>((const double*)L.data + j * L.ld);
+      const double2* rs = reinterpret_cast<const double2*>(rho_d);
+      double s = 0.0;
+      const int nv = ldN >> 1;
+      for (int k = lane; k < nv; k += 32) {
+        double2 a = __ldg(row + k);
+        double2 r = rs[k];
+        s = fma(a.x, r.x, s);
+        s = fma(a.y, r.y, s);
+      }
+      return warp_sum(s);
+    }
+    case LK_F32D: {
+      const float4* row = reinterpret_cast<const float4*>((const float*)L.data + j * L.ld);
+      const double2* rs = reinterpret_cast<const double2*>(rho_d);
+      double s = 0.0;
+      const int nv = ldN >> 2;
+      for (int k = lane; k < nv; k += 32) {
+        float4 a = __ldg(row + k);
+        double2 r0 = rs[2 * k], r1 = rs[2 * k + 1];
+        s = fma((double)a.x, r0.x, s);
+        s = fma((double)a.y, r0.y, s);
+        s = fma((double)a.z, r1.x, s);
+        s = fma((double)a.w, r1.y, s);
+      }
+      return warp_sum(s);
+    }
+  }
+  return 0.0;
+}
+
+// Four consecutive rows [r0, r0 + 4) of atom j (r0 a multiple of 4), as FP32 / FP64.
+__device__ __forceinline__ float4 load4_f(const LevelDev& L, int64_t j, int r0) {
+  switch (L.kind) {
+    case LK_F32:
+      return __ldg(reinterpret_cast<const float4*>((const float*)L.data + j * L.ld + r0));
+    case LK_BF16: {
+      uint2 v = __ldg(reinterpret_cast<const uint2*>((const __nv_bfloat16*)L.data + j * L.ld + r0));
+      float2 a = bf16x2_to_f2(v.x), b = bf16x2_to_f2(v.y);
+      return make_float4(a.x, a.y, b.x, b.y);
+    }
+    case LK_FP8: {
+      uint32_t v = __ldg(reinterpret_cast<const unsigned int*>((const uint8_t*)L.data + j * L.ld + r0));
+      float2 a = fp8x2_to_f2((uint16_t)(v & 0xffffu)), b = fp8x2_to_f2((uint16_t)(v >> 16));
+      return make_float4(a.x, a.y, b.x, b.y);
+    }
+  }
+  return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+struct D4 {
+  double x, y, z, w;
+};
+
+__device__ __forceinline__ D4 load4_d(const LevelDev& L, int64_t j, int r0) {
+  if (L.kind == LK_F64) {
+    const double2* p = reinterpret_cast<const double2*>((const double*)L.data + j * L.ld + r0);
+    double2 a = __ldg(p), b = __ldg(p + 1);
+    return D4{a.x, a.y, b.x, b.y};
+  }
+  float4 f = __ldg(reinterpret_cast<const float4*>((const float*)L.data + j * L.ld + r0));
+  return D4{f.x, f.y, f.z, f.w};
+}
+
+}  // namespace lasso

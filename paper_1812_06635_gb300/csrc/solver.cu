@@ -1,0 +1,1437 @@
+// The screened FISTA solve on the device: one pass = residual -> correlation fused with the
+// proximal update and partial reductions -> gap / dual scaling / stable safe test / switch /
+// ordered compaction of the preserved set -> work-item schedule.  Passes are captured in a
+// CUDA graph and replayed until every signal has stopped.
+//
+// Paper: Algorithm 1 (FastL1) and Algorithm 2 (SwitchDictionary); dual points
+// eq:theta_dynamic_approx; stable GAP Safe sphere Theorem 1 / Table I; gap ratio
+// eq:DefRatioSwitch; look-ahead estimate eq:DefCardinalEstimated; ISTA update
+// eq:ISTA_update (FISTA momentum of Beck & Teboulle); stopping rule of Section IV.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "dict.cuh"
+#include "kernels.cuh"
+
+namespace lasso {
+
+constexpr int SCREEN_THREADS = 512;
+constexpr int CORR_THREADS = 256;
+constexpr int RES_ROWS = RES_THREADS * 4;   // rows per residual block
+constexpr int GEMM_T = 64;                  // tile of the Kronecker small GEMMs
+
+struct Workspace {
+  int64_t B = 0, K = 0, ldN = 0;
+  bool vt_double = false;
+  bool kron = false;
+  int R = 0, N1 = 0, K1 = 0, N2 = 0, K2 = 0;
+  void* Yw = nullptr;
+  void* Rho = nullptr;
+  void* X = nullptr;
+  void* Z = nullptr;
+  void* G = nullptr;
+  void* Xout = nullptr;
+  void* nz_val = nullptr;
+  int32_t* nz_idx = nullptr;
+  int32_t* kept = nullptr;           // 2 x B x K
+  float* c0ub = nullptr;             // B x K, |a_j^T y| upper bounds (Dynamic Safe rule)
+  double* part_res = nullptr;        // B x nrb x 2
+  double* part_corr = nullptr;       // B x nch x 2
+  int32_t* offsets = nullptr;        // B + 1
+  int32_t* counters = nullptr;       // [0] done count
+  double* alg_bytes = nullptr;       // [6] algorithmic bytes per kernel kind
+  SigState* st = nullptr;
+  // Kronecker scratch
+  float* Gfull = nullptr;            // B x K
+  float* AZ = nullptr;               // B x ldN
+  float* Xd = nullptr;               // B x K
+  float* Tk = nullptr;               // B x R x max(K1 N2, N1 K2)
+  int32_t* h_counters = nullptr;     // pinned
+  cudaStream_t stream = nullptr;     // used when the caller passes the legacy default stream
+  int nrb = 0, nch = 0;
+};
+
+void free_ws(Workspace* w) {
+  if (!w) return;
+  void* ptrs[] = {w->Yw, w->Rho, w->X, w->Z, w->G, w->Xout, w->nz_val, w->nz_idx, w->kept, w->c0ub,
+                  w->part_res, w->part_corr, w->offsets, w->counters, w->alg_bytes, w->st, w->Gfull, w->AZ, w->Xd, w->Tk};
+  for (void* p : ptrs) cudaFree(p);
+  cudaFreeHost(w->h_counters);
+  if (w->stream) cudaStreamDestroy(w->stream);
+  delete w;
+}
+
+static int ws_alloc(void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
+    return LASSO_ERR_NOMEM;
+  }
+  return LASSO_OK;
+}
+
+static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
+  Workspace* w = d->ws;
+  if (w && w->B >= B && w->vt_double == vt_double) {
+    *out = w;
+    return LASSO_OK;
+  }
+  if (w) free_ws(w);
+  d->ws = nullptr;
+  w = new Workspace();
+  w->B = B;
+  w->K = d->K;
+  w->ldN = d->ldN;
+  w->vt_double = vt_double;
+  w->kron = d->is_kron;
+  w->R = d->R;
+  w->N1 = d->N1;
+  w->K1 = d->K1;
+  w->N2 = d->N2;
+  w->K2 = d->K2;
+  w->nrb = (int)((d->N + RES_ROWS - 1) / RES_ROWS);
+  w->nch = (int)((d->K + CORR_CHUNK - 1) / CORR_CHUNK);
+  const size_t vs = vt_double ? 8 : 4;
+  const size_t BK = (size_t)B * d->K, BN = (size_t)B * d->ldN;
+  int rc = 0;
+  rc |= ws_alloc(&w->Yw, BN * vs);
+  rc |= ws_alloc(&w->Rho, BN * vs);
+  rc |= ws_alloc(&w->X, BK * vs);
+  rc |= ws_alloc(&w->Z, BK * vs);
+  rc |= ws_alloc(&w->G, BK * vs);
+  rc |= ws_alloc(&w->Xout, BK * vs);
+  rc |= ws_alloc(&w->nz_val, BK * vs);
+  rc |= ws_alloc((void**)&w->nz_idx, BK * 4);
+  rc |= ws_alloc((void**)&w->kept, 2 * BK * 4);
+  rc |= ws_alloc((void**)&w->c0ub, BK * 4);
+  rc |= ws_alloc((void**)&w->part_res, (size_t)B * w->nrb * 2 * 8);
+  rc |= ws_alloc((void**)&w->part_corr, (size_t)B * w->nch * 2 * 8);
+  rc |= ws_alloc((void**)&w->offsets, (size_t)(B + 1) * 4);
+  rc |= ws_alloc((void**)&w->counters, 64);
+  rc |= ws_alloc((void**)&w->alg_bytes, 16 * sizeof(double));   // [0,6) bytes, [8,16) atom-passes per level
+  rc |= ws_alloc((void**)&w->st, (size_t)B * sizeof(SigState));
+  if (d->is_kron) {
+    const size_t tk = (size_t)B * d->R * std::max<int64_t>((int64_t)d->K1 * d->N2, (int64_t)d->N1 * d->K2);
+    rc |= ws_alloc((void**)&w->Gfull, BK * 4);
+    rc |= ws_alloc((void**)&w->AZ, BN * 4);
+    rc |= ws_alloc((void**)&w->Xd, BK * 4);
+    rc |= ws_alloc((void**)&w->Tk, tk * 4);
+  }
+  if (cudaHostAlloc((void**)&w->h_counters, 64, cudaHostAllocDefault) != cudaSuccess) rc |= 1;
+  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) rc |= 1;
+  if (rc) {
+    free_ws(w);
+    return LASSO_ERR_NOMEM;
+  }
+  d->ws = w;
+  *out = w;
+  return LASSO_OK;
+}
+
+// Pointers of the current pass (kernel parameter block).
+template <typename VT>
+struct PassArgs {
+  DictDev dd;
+  SolveParams sp;
+  const VT* Yw;
+  VT* Rho;
+  VT* X;
+  VT* Z;
+  VT* G;
+  VT* Xout;
+  VT* nz_val;
+  int32_t* nz_idx;
+  int32_t* kept;
+  float* c0ub;
+  double* part_res;
+  double* part_corr;
+  int32_t* offsets;
+  int32_t* counters;
+  double* alg_bytes;
+  SigState* st;
+  float* Gfull;
+  float* AZ;
+  float* Xd;
+  float* Tk;
+  int64_t K, ldN;
+  int nrb, nch;
+};
+
+__device__ __forceinline__ double level_elem_bytes(int kind) {
+  switch (kind) {
+    case LK_F64: return 8.0;
+    case LK_F32:
+    case LK_F32D: return 4.0;
+    case LK_BF16: return 2.0;
+    case LK_FP8: return 1.0;
+  }
+  return 0.0;
+}
+
+template <typename VT>
+__device__ __forceinline__ int32_t* kept_of(const PassArgs<VT>& a, int b, int parity) {
+  return a.kept + ((int64_t)parity * a.sp.B + b) * a.K;
+}
+
+// ------------------------------------------------------------------ init
+
+// ||y||^2, ||y||, FISTA scalars; the preserved set starts as every atom.
+template <typename VT>
+__global__ void k_init_state(PassArgs<VT> a, const double* __restrict__ lambdas) {
+  const int b = blockIdx.x;
+  const VT* y = a.Yw + (int64_t)b * a.ldN;
+  double s = 0.0;
+  for (int n = threadIdx.x; n < a.dd.N; n += blockDim.x) s = fma((double)y[n], (double)y[n], s);
+  __shared__ double sh[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  int32_t* kp = kept_of(a, b, 0);
+  for (int64_t j = threadIdx.x; j < a.K; j += blockDim.x) kp[j] = (int32_t)j;
+  if (threadIdx.x == 0) {
+    double yy = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) yy += sh[w];
+    SigState st;
+    memset(&st, 0, sizeof(st));
+    st.lam = lambdas[b];
+    st.yy = yy;
+    st.ynorm = sqrt(yy);
+    st.t = 1.0;
+    st.beta = 0.0;
+    st.level = 0;
+    st.n_kept = (int)a.K;
+    st.n_chunks = (int)((a.K + CORR_CHUNK - 1) / CORR_CHUNK);
+    st.gap = INFINITY;
+    st.status = LASSO_OK;
+    if (!(yy < INFINITY) || !(st.lam == st.lam)) {
+      st.status = LASSO_ERR_NONFINITE;
+      st.done = 1;
+    } else if (yy == 0.0) {
+      st.done = 1;         // y = 0: x* = 0 with gap 0
+      st.gap = 0.0;
+      st.n_kept = 0;
+    }
+    a.st[b] = st;
+  }
+}
+
+// Prefix sum of the correlation work items of the live signals, and the done count.
+template <typename VT>
+__global__ void k_schedule(PassArgs<VT> a) {
+  __shared__ int sh_sum[32];
+  __shared__ int sh_done[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  int done_total = 0;
+  __syncthreads();
+  const int B = a.sp.B;
+  for (int base = 0; base < B; base += blockDim.x) {
+    int b = base + threadIdx.x;
+    int items = 0, dn = 0;
+    if (b < B) {
+      const SigState& s = a.st[b];
+      dn = s.done;
+      items = s.done ? 0 : s.n_chunks;
+    }
+    // block exclusive scan of items
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int v = items;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    int dsum = warp_sum_i(dn);
+    if (lane == 31) sh_sum[wid] = v;
+    if (lane == 0) sh_done[wid] = dsum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int nw = blockDim.x >> 5;
+      int x = threadIdx.x < nw ? sh_sum[threadIdx.x] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)threadIdx.x >= o) x += t;
+      }
+      sh_sum[threadIdx.x] = x;   // inclusive over warps
+    }
+    __syncthreads();
+    int warp_off = wid ? sh_sum[wid - 1] : 0;
+    if (b < B) a.offsets[b] = carry + warp_off + v - items;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) done_total += sh_done[w];
+    __syncthreads();
+    if (threadIdx.x == 0) carry += sh_sum[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.offsets[B] = carry;
+    a.counters[0] = done_total;
+  }
+}
+
+// ------------------------------------------------------------------ residual (dense levels)
+
+// rho^_b = y_b - sum_{j in nz(z_b)} z_bj a~_j over 4 rows per thread, plus ||rho^||^2 and y^T rho^.
+template <typename VT>
+__global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
+  const int b = blockIdx.y;
+  const SigState& s = a.st[b];
+  if (s.done) return;
+  const LevelDev& L = a.dd.lv[s.level];
+  const int r0 = (blockIdx.x * RES_THREADS + threadIdx.x) * 4;
+  const VT* y = a.Yw + (int64_t)b * a.ldN;
+  VT* rho = a.Rho + (int64_t)b * a.ldN;
+  __shared__ int32_t s_idx[RES_THREADS];
+  __shared__ double s_val[RES_THREADS];
+  __shared__ double s_red[2][RES_THREADS / 32];
+  const bool active = r0 < a.dd.N;
+  const bool writer = r0 < a.ldN;
+  double out[4] = {0.0, 0.0, 0.0, 0.0};
+  if (L.kind == LK_KRON) {
+    // structured product already formed: rho = y - (A~ z)
+    if (active) {
+      const float* az = a.AZ + (int64_t)b * a.ldN;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[v] = (double)y[r0 + v] - (double)az[r0 + v];
+    }
+  } else if (level_fp64_arith(L.kind)) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int nnz = s.n_nz;
+    for (int base = 0; base < nnz; base += RES_THREADS) {
+      __syncthreads();
+      if (base + threadIdx.x < nnz) {
+        s_idx[threadIdx.x] = a.nz_idx[(int64_t)b * a.K + base + threadIdx.x];
+        s_val[threadIdx.x] = (double)a.nz_val[(int64_t)b * a.K + base + threadIdx.x];
+      }
+      __syncthreads();
+      const int cnt = min(RES_THREADS, nnz - base);
+      if (active)
+        for (int q = 0; q < cnt; ++q) {
+          D4 av = load4_d(L, s_idx[q], r0);
+          double w = s_val[q];
+          acc[0] = fma(w, av.x, acc[0]);
+          acc[1] = fma(w, av.y, acc[1]);
+          acc[2] = fma(w, av.z, acc[2]);
+          acc[3] = fma(w, av.w, acc[3]);
+        }
+    }
+    if (active)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[v] = (double)y[r0 + v] - acc[v];
+  } else {
+    DF acc[4];
+    float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v].init();
+    const int nnz = s.n_nz;
+    int parity = 0;
+    for (int base = 0; base < nnz; base += RES_THREADS) {
+      __syncthreads();
+      if (base + threadIdx.x < nnz) {
+        int32_t j = a.nz_idx[(int64_t)b * a.K + base + threadIdx.x];
+        float w = (float)a.nz_val[(int64_t)b * a.K + base + threadIdx.x];
+        if (L.kind == LK_FP8) w = __fmul_rn(w, L.scale[j]);
+        s_idx[threadIdx.x] = j;
+        s_val[threadIdx.x] = (double)w;
+      }
+      __syncthreads();
+      const int cnt = min(RES_THREADS, nnz - base);
+      if (active && L.kind == LK_F32) {
+        for (int q = 0; q < cnt; ++q) {
+          float4 av = load4_f(L, s_idx[q], r0);
+          float w = (float)s_val[q];
+          dot2_add(acc[0], w, av.x);
+          dot2_add(acc[1], w, av.y);
+          dot2_add(acc[2], w, av.z);
+          dot2_add(acc[3], w, av.w);
+        }
+      } else if (active)
+        for (int q = 0; q < cnt; ++q) {
+          float4 av = load4_f(L, s_idx[q], r0);
+          float w = (float)s_val[q];
+          if (parity == 0) {
+            p[0] = __fmul_rn(w, av.x);
+            p[1] = __fmul_rn(w, av.y);
+            p[2] = __fmul_rn(w, av.z);
+            p[3] = __fmul_rn(w, av.w);
+          } else {
+            acc[0].add(__fmaf_rn(w, av.x, p[0]));
+            acc[1].add(__fmaf_rn(w, av.y, p[1]));
+            acc[2].add(__fmaf_rn(w, av.z, p[2]));
+            acc[3].add(__fmaf_rn(w, av.w, p[3]));
+          }
+          parity ^= 1;
+        }
+    }
+    if (active) {
+      if (parity) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v].add(p[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[v] = (double)y[r0 + v] - acc[v].value();
+    }
+  }
+  double rr = 0.0, yr = 0.0;
+  if (writer) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (r0 + v < a.dd.N) {
+        VT r = (VT)out[v];
+        rho[r0 + v] = r;
+        rr = fma((double)r, (double)r, rr);
+        yr = fma((double)y[r0 + v], (double)r, yr);
+      } else {
+        rho[r0 + v] = (VT)0;
+      }
+    }
+  }
+  rr = warp_sum(rr);
+  yr = warp_sum(yr);
+  if ((threadIdx.x & 31) == 0) {
+    s_red[0][threadIdx.x >> 5] = rr;
+    s_red[1][threadIdx.x >> 5] = yr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int w = 0; w < RES_THREADS / 32; ++w) {
+      t0 += s_red[0][w];
+      t1 += s_red[1][w];
+    }
+    double* pr = a.part_res + ((int64_t)b * a.nrb + blockIdx.x) * 2;
+    pr[0] = t0;
+    pr[1] = t1;
+    if (a.alg_bytes && blockIdx.x == 0 && L.kind != LK_KRON) {
+      // nonzero atoms of z (rows of A~), their values and indices, y read and rho written
+      const double vs = (double)sizeof(VT);
+      atomicAdd(&a.alg_bytes[0], (double)s.n_nz * ((double)a.dd.N * level_elem_bytes(L.kind) + 4.0 + vs) +
+                                     2.0 * a.dd.N * vs);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ correlation + update
+
+enum CorrMode { CORR_PASS = 0, CORR_INIT = 1, CORR_CERT = 2 };
+
+// Correlations g_j = a~_j^T rho^ over one chunk of the preserved list, fused with the FISTA
+// update of the chunk's coefficients and with the chunk's maxima max(|g_j| + eps_j ||rho||)
+// and max |g_j| (the two dual scalings).  Persistent grid over (signal, chunk) items.
+// CORR_INIT: rho := y over every atom with the most precise level (lambda_max, a^T y bounds).
+// CORR_CERT: every atom with the most precise level, no update (full-dictionary certificate).
+template <typename VT, int MODE>
+__global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double s_m1[CORR_THREADS / 32], s_m2[CORR_THREADS / 32];
+  __shared__ double s_nrho;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int B = a.sp.B;
+  const int total = a.offsets[B];
+  const int ldN = (int)a.ldN;
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    // signal of this item: last b with offsets[b] <= item
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (a.offsets[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const int b = lo;
+    const int chunk = item - a.offsets[b];
+    const SigState& s = a.st[b];
+    const int lvl = MODE == CORR_PASS ? s.level : a.dd.n_levels - 1;
+    const LevelDev& L = a.dd.lv[lvl];
+    const bool fp64a = level_fp64_arith(L.kind);
+    const int npos = MODE == CORR_PASS ? s.n_kept : (int)a.K;
+    const int p0 = chunk * CORR_CHUNK, p1 = min(npos, p0 + CORR_CHUNK);
+    const VT* src = (MODE == CORR_INIT ? a.Yw : a.Rho) + (int64_t)b * a.ldN;
+    __syncthreads();
+    // stage rho (or y) in shared memory
+    if (L.kind != LK_KRON) {
+      if (fp64a) {
+        double* rd = reinterpret_cast<double*>(smem_raw);
+        for (int n = threadIdx.x; n < ldN; n += CORR_THREADS) rd[n] = (double)src[n];
+      } else {
+        float* rf = reinterpret_cast<float*>(smem_raw);
+        for (int n = threadIdx.x; n < ldN; n += CORR_THREADS) rf[n] = (float)src[n];
+      }
+    }
+    if (threadIdx.x == 0) {
+      double rr = 0.0;
+      if (MODE == CORR_INIT) {
+        rr = s.yy;
+      } else {
+        for (int q = 0; q < a.nrb; ++q) rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
+      }
+      s_nrho = sqrt(rr);
+    }
+    __syncthreads();
+    const double nrho = s_nrho;
+    const double ug = fp64a && sizeof(VT) == 8 ? U64 : U32;
+    const double inv_L = 1.0 / a.sp.L;
+    const double thr = s.lam * inv_L;
+    const int32_t* kp = kept_of(a, b, s.parity);
+    VT* X = a.X + (int64_t)b * a.K;
+    VT* Z = a.Z + (int64_t)b * a.K;
+    VT* G = a.G + (int64_t)b * a.K;
+    double m1 = 0.0, m2 = 0.0;
+    for (int pos = p0 + wid; pos < p1; pos += CORR_THREADS / 32) {
+      const int64_t j = MODE == CORR_PASS ? kp[pos] : pos;
+      double g;
+      if (L.kind == LK_KRON) {
+        g = (double)a.Gfull[(int64_t)b * a.K + j];
+      } else {
+        g = warp_atom_dot(L, j, ldN, reinterpret_cast<const float*>(smem_raw),
+                          reinterpret_cast<const double*>(smem_raw), lane);
+      }
+      if (lane == 0) {
+        const double ga = fabs(g) * (1.0 + 3.0 * ug);
+        const double epsr = L.eps[j] + L.gam_corr * L.kappa[j];
+        m1 = fmax(m1, ga + epsr * nrho);
+        m2 = fmax(m2, fabs(g));
+        if (MODE == CORR_INIT) {
+          if (a.c0ub) a.c0ub[(int64_t)b * a.K + j] = __double2float_ru(ga + epsr * nrho);
+        } else if (MODE == CORR_PASS) {
+          const double xj = (double)X[j];
+          const double zj = (double)Z[j];
+          const double v = zj + g * inv_L;
+          const double xn = v > thr ? v - thr : (v < -thr ? v + thr : 0.0);
+          const double zn = a.sp.algo == LASSO_FISTA ? xn + s.beta * (xn - xj) : xn;
+          X[j] = (VT)xn;
+          Z[j] = (VT)zn;
+          G[pos] = (VT)g;
+        }
+      }
+    }
+    if (lane == 0) {
+      s_m1[wid] = m1;
+      s_m2[wid] = m2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t1 = 0.0, t2 = 0.0;
+      for (int w = 0; w < CORR_THREADS / 32; ++w) {
+        t1 = fmax(t1, s_m1[w]);
+        t2 = fmax(t2, s_m2[w]);
+      }
+      double* pc = a.part_corr + ((int64_t)b * a.nch + chunk) * 2;
+      pc[0] = t1;
+      pc[1] = t2;
+      if (MODE == CORR_PASS && a.alg_bytes && L.kind != LK_KRON) {
+        // preserved atoms of the chunk (rows of A~, index, x and z read and written, g written),
+        // plus rho once per signal
+        const double vs = (double)sizeof(VT);
+        atomicAdd(&a.alg_bytes[1], (double)(p1 - p0) * ((double)a.dd.N * level_elem_bytes(L.kind) + 4.0 + 5.0 * vs) +
+                                       (chunk == 0 ? a.dd.N * vs : 0.0));
+      }
+    }
+  }
+}
+
+// lambda_max bounds, lambda, early exit when lambda >= lambda_max (x* = 0, gap 0).
+template <typename VT>
+__global__ void k_init_finish(PassArgs<VT> a, int lambda_relative) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.sp.B) return;
+  SigState& s = a.st[b];
+  if (s.done) return;
+  double ub = 0.0, lb = 0.0;
+  const int nch = (int)((a.K + CORR_CHUNK - 1) / CORR_CHUNK);
+  for (int c = 0; c < nch; ++c) {
+    ub = fmax(ub, a.part_corr[((int64_t)b * a.nch + c) * 2]);
+    lb = fmax(lb, a.part_corr[((int64_t)b * a.nch + c) * 2 + 1]);
+  }
+  s.lam_max_lb = lb;
+  s.lam_max_ub = ub;
+  if (lambda_relative) s.lam = s.lam * lb;
+  if (!(s.lam > 0.0) || !(s.lam < INFINITY)) {
+    s.status = LASSO_ERR_INVALID_ARG;
+    s.done = 1;
+    return;
+  }
+  if (s.lam >= ub) {
+    s.done = 1;
+    s.gap = 0.0;
+    s.n_kept = 0;
+    s.status = LASSO_OK;
+  }
+  s.n_chunks = (int)((s.n_kept + CORR_CHUNK - 1) / CORR_CHUNK);
+}
+
+// ------------------------------------------------------------------ gap, screening, switch
+
+// One block per signal.  Thread 0 evaluates the FP64 scalars of the pass:
+//   P = 1/2||rho||^2 + lam ||z||_1, theta' = s' rho (stable scaling), theta~ = s~ rho,
+//   G' = P - D(theta'), G~ = P - D(theta~), delta = ||rho|| e + e^2/2 with
+//   e = sum eps_j |z_j| + (residual rounding), R' = sqrt(2 G' + 2 delta) / lam,
+//   gamma = G~ / G', stop when the level is exact and (G' + delta) / ||y||^2 <= tol.
+// Then every preserved atom is tested (stable GAP or Dynamic Safe sphere), K_t is counted,
+// Algorithm 2 picks the next level, and the preserved list, the nonzero list of z+ and their
+// sums are compacted in order.
+template <typename VT>
+__global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
+  const int b = blockIdx.x;
+  SigState* sp = a.st + b;
+  if (sp->done) return;
+  __shared__ double sc[16];
+  __shared__ int si[8];
+  __shared__ int s_warp[SCREEN_THREADS / 32];
+  __shared__ int s_warp2[SCREEN_THREADS / 32];
+  __shared__ double s_red[3][SCREEN_THREADS / 32];
+  const int I = a.dd.n_levels - 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    SigState s = *sp;
+    const LevelDev& L = a.dd.lv[s.level];
+    double rr = 0.0, yr = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int q = 0; q < a.nrb; ++q) {
+      rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
+      yr += a.part_res[((int64_t)b * a.nrb + q) * 2 + 1];
+    }
+    for (int c = 0; c < s.n_chunks; ++c) {
+      m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
+      m2 = fmax(m2, a.part_corr[((int64_t)b * a.nch + c) * 2 + 1]);
+    }
+    const double lam = s.lam;
+    const double nrho = sqrt(rr);
+    const double e_r = residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8);
+    const double e = s.sum_epsz + e_r;
+    double sp_ = 0.0, st_ = 0.0;
+    if (rr > 0.0) {
+      const double beta = yr / (lam * rr);
+      sp_ = m1 > 0.0 ? fmin(fmax(beta, -1.0 / m1), 1.0 / m1) : beta;
+      st_ = m2 > 0.0 ? fmin(fmax(beta, -1.0 / m2), 1.0 / m2) : beta;
+    }
+    const double P = 0.5 * rr + lam * s.l1;
+    const double Dp = lam * sp_ * yr - 0.5 * lam * lam * sp_ * sp_ * rr;
+    const double Dt = lam * st_ * yr - 0.5 * lam * lam * st_ * st_ * rr;
+    const double Gp = P - Dp, Gt = P - Dt;
+    const double delta = nrho * e + 0.5 * e * e;
+    const double Rp = sqrt(fmax(2.0 * Gp + 2.0 * delta, 0.0)) / lam;
+    const double Rt = sqrt(fmax(2.0 * Gt, 0.0)) / lam;
+    const double gamma = Gp > 0.0 ? Gt / Gp : 0.0;
+    const double gcert = fmax(Gp + delta, 0.0) / s.yy;
+    s.iters += 1;
+    s.level_passes[s.level] += 1;
+    if (a.alg_bytes) atomicAdd(&a.alg_bytes[8 + s.level], (double)s.n_kept);
+    s.Gp = Gp;
+    s.Gt = Gt;
+    s.gamma = gamma;
+    s.Rp = Rp;
+    s.delta = delta;
+    s.sp = sp_;
+    int action = 0;   // 0 continue, 1 stop (converged), 2 stop (error)
+    if (!(rr < INFINITY) || !(yr == yr) || !(m1 < INFINITY) || !(Gp == Gp) || !(delta < INFINITY)) {
+      s.status = LASSO_ERR_NONFINITE;
+      action = 2;
+    } else if (s.level == I && gcert <= a.sp.tol) {
+      s.status = LASSO_OK;
+      action = 1;
+    } else if (s.iters >= a.sp.max_iter) {
+      s.status = LASSO_ERR_MAXITER;
+      action = 2;
+    }
+    if (s.level == I || action) s.gap = gcert;
+    // Dynamic Safe radius ||theta' - y/lam|| (Table I)
+    const double d2 = sp_ * sp_ * rr - 2.0 * sp_ * yr / lam + s.yy / (lam * lam);
+    const bool screen = rr > 0.0 && (s.iters % a.sp.screen_every) == 0;
+    sc[0] = fabs(sp_);
+    sc[1] = fabs(sp_) * nrho;
+    sc[2] = a.sp.rule == LASSO_RULE_GAP ? Rp : sqrt(fmax(d2, 0.0));
+    sc[3] = fabs(st_);
+    sc[4] = Rt;
+    sc[5] = 1.0 - a.sp.tau;
+    sc[6] = 1.0 + 3.0 * (level_fp64_arith(L.kind) && sizeof(VT) == 8 ? U64 : U32);
+    sc[7] = 1.0 / lam;
+    si[0] = action;
+    si[1] = screen ? 1 : 0;
+    *sp = s;
+  }
+  __syncthreads();
+  const int action = si[0];
+  SigState s = *sp;
+  const int32_t* kp = kept_of(a, b, s.parity);
+  VT* X = a.X + (int64_t)b * a.K;
+  VT* Z = a.Z + (int64_t)b * a.K;
+  const VT* G = a.G + (int64_t)b * a.K;
+  if (action) {
+    // return the certified point z_t (its nonzero list) and stop
+    VT* xo = a.Xout + (int64_t)b * a.K;
+    for (int q = threadIdx.x; q < s.n_nz; q += SCREEN_THREADS)
+      xo[a.nz_idx[(int64_t)b * a.K + q]] = a.nz_val[(int64_t)b * a.K + q];
+    if (threadIdx.x == 0) sp->done = 1;
+    return;
+  }
+  const LevelDev& L = a.dd.lv[s.level];
+  const bool screen = si[1];
+  const double abs_sp = sc[0], c_eps = sc[1], Rs = sc[2], abs_st = sc[3], Rt = sc[4], thr = sc[5], gfac = sc[6],
+               inv_lam = sc[7];
+  const bool gap_rule = a.sp.rule == LASSO_RULE_GAP;
+  const double* anorm = a.dd.anorm;
+  const float* c0 = a.c0ub + (int64_t)b * a.K;
+  auto keep_of = [&](int pos, int64_t j) -> bool {
+    if (!screen) return true;
+    double mu;
+    if (gap_rule) mu = abs_sp * fabs((double)G[pos]) * gfac + (L.eps[j] + L.gam_corr * L.kappa[j]) * c_eps + Rs * anorm[j];
+    else mu = (double)c0[j] * inv_lam + Rs * anorm[j];
+    return mu >= thr;
+  };
+  // ---- phase 1: look-ahead estimate K_t (conventional test on A~, eq:DefCardinalEstimated)
+  int kt = 0;
+  for (int pos = threadIdx.x; pos < s.n_kept; pos += SCREEN_THREADS) {
+    const int64_t j = kp[pos];
+    if (abs_st * fabs((double)G[pos]) + Rt * (double)L.atnorm[j] >= 1.0) ++kt;
+  }
+  kt = warp_sum_i(kt);
+  if (lane == 0) s_warp[wid] = kt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < SCREEN_THREADS / 32; ++w) t += s_warp[w];
+    // Algorithm 2
+    int nl = s.level;
+    if (s.level < I) {
+      if (t <= L.rc * (double)a.K) nl = I;
+      else if (s.gamma <= a.sp.Gamma) nl = s.level + 1;
+    }
+    si[2] = nl;
+    si[3] = t;
+  }
+  __syncthreads();
+  const int new_level = si[2];
+  const LevelDev& Ln = a.dd.lv[new_level];
+  // ---- phase 2: ordered compaction of the preserved list and of the nonzeros of z+
+  int32_t* kn = kept_of(a, b, s.parity ^ 1);
+  int32_t* nzi = a.nz_idx + (int64_t)b * a.K;
+  VT* nzv = a.nz_val + (int64_t)b * a.K;
+  int base_k = 0, base_z = 0;
+  double l1 = 0.0, se = 0.0, sk = 0.0;
+  for (int t0 = 0; t0 < s.n_kept; t0 += SCREEN_THREADS) {
+    const int pos = t0 + threadIdx.x;
+    bool keep = false, nz = false;
+    int64_t j = 0;
+    double zv = 0.0;
+    if (pos < s.n_kept) {
+      j = kp[pos];
+      keep = keep_of(pos, j);
+      if (!keep) {
+        X[j] = (VT)0;
+        Z[j] = (VT)0;
+      } else {
+        zv = (double)Z[j];
+        nz = zv != 0.0;
+      }
+    }
+    const unsigned bk = __ballot_sync(0xffffffffu, keep);
+    const unsigned bz = __ballot_sync(0xffffffffu, nz);
+    if (lane == 0) {
+      s_warp[wid] = __popc(bk);
+      s_warp2[wid] = __popc(bz);
+    }
+    __syncthreads();
+    int off_k = base_k, off_z = base_z, tot_k = 0, tot_z = 0;
+    for (int w = 0; w < SCREEN_THREADS / 32; ++w) {
+      if (w < wid) {
+        off_k += s_warp[w];
+        off_z += s_warp2[w];
+      }
+      tot_k += s_warp[w];
+      tot_z += s_warp2[w];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    if (keep) kn[off_k + __popc(bk & below)] = (int32_t)j;
+    if (nz) {
+      const int q = off_z + __popc(bz & below);
+      nzi[q] = (int32_t)j;
+      nzv[q] = (VT)zv;
+      const double az = fabs(zv);
+      l1 += az;
+      se = fma(Ln.eps[j], az, se);
+      sk = fma(Ln.kappa[j], az, sk);
+    }
+    base_k += tot_k;
+    base_z += tot_z;
+    __syncthreads();
+  }
+  l1 = warp_sum(l1);
+  se = warp_sum(se);
+  sk = warp_sum(sk);
+  if (lane == 0) {
+    s_red[0][wid] = l1;
+    s_red[1][wid] = se;
+    s_red[2][wid] = sk;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    for (int w = 0; w < SCREEN_THREADS / 32; ++w) {
+      t1 += s_red[0][w];
+      t2 += s_red[1][w];
+      t3 += s_red[2][w];
+    }
+    SigState& o = *sp;
+    o.l1 = t1;
+    o.sum_epsz = t2;
+    o.sum_kapz = t3;
+    o.n_kept = base_k;
+    o.n_nz = base_z;
+    o.Kt = si[3];
+    o.level = new_level;
+    o.parity = s.parity ^ 1;
+    o.n_chunks = (base_k + CORR_CHUNK - 1) / CORR_CHUNK;
+    // FISTA: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, momentum (t_k - 1) / t_{k+1} for the next update
+    const double t1n = 0.5 * (1.0 + sqrt(1.0 + 4.0 * s.t * s.t));
+    const double t2n = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t1n * t1n));
+    o.t = t1n;
+    o.beta = (t1n - 1.0) / t2n;
+  }
+}
+
+// ------------------------------------------------------------------ Kronecker levels
+
+// Batched FP32 GEMM tile: C[bz](m, n) (+)= sum_{r < R} sum_k A(bz, r, m, k) B(bz, r, k, n).
+// The four Kronecker stages instantiate it with their index maps (row-major vectorisation).
+enum KronStage { KS_T = 0, KS_G = 1, KS_U = 2, KS_Y = 3 };
+
+template <typename VT, int STAGE>
+__global__ void __launch_bounds__(256) k_kron_gemm(PassArgs<VT> a) {
+  // batch index: blockIdx.z = b * Rb + r (stages T, U) or b (stages G, Y)
+  int b, r = 0;
+  const LevelDev* Lp;
+  int Rmax = 0;
+  {
+    int bz = blockIdx.z;
+    for (int l = 0; l < a.dd.n_levels; ++l)
+      if (a.dd.lv[l].kind == LK_KRON) Rmax = max(Rmax, a.dd.lv[l].R);
+    if (STAGE == KS_T || STAGE == KS_U) {
+      b = bz / Rmax;
+      r = bz % Rmax;
+    } else {
+      b = bz;
+    }
+    const SigState& s = a.st[b];
+    if (s.done) return;
+    Lp = &a.dd.lv[s.level];
+    if (Lp->kind != LK_KRON) return;
+    if (r >= Lp->R) return;
+  }
+  const LevelDev& L = *Lp;
+  const int N1 = L.N1, K1 = L.K1, N2 = L.N2, K2 = L.K2, R = L.R;
+  int M, Nc, Kd;
+  if (STAGE == KS_T) { M = K1; Nc = N2; Kd = N1; }
+  else if (STAGE == KS_G) { M = K1; Nc = K2; Kd = N2; }
+  else if (STAGE == KS_U) { M = N1; Nc = K2; Kd = K1; }
+  else { M = N1; Nc = N2; Kd = K2; }
+  const int m0 = blockIdx.y * GEMM_T, n0 = blockIdx.x * GEMM_T;
+  if (m0 >= M || n0 >= Nc) return;
+  const int64_t TK = (int64_t)Rmax * max(K1 * N2, N1 * K2);   // same stride for every signal
+  float* Tb = a.Tk + (int64_t)b * TK;
+  __shared__ float sA[16][GEMM_T + 4];
+  __shared__ float sB[16][GEMM_T + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  const int nr = (STAGE == KS_G || STAGE == KS_Y) ? R : 1;
+  for (int rr = 0; rr < nr; ++rr) {
+    const int rx = (STAGE == KS_G || STAGE == KS_Y) ? rr : r;
+    for (int k0 = 0; k0 < Kd; k0 += 16) {
+      // load A tile (16 x 64) and B tile (16 x 64)
+      for (int e = threadIdx.x; e < 16 * GEMM_T; e += 256) {
+        const int kk = e / GEMM_T, mm = e % GEMM_T;
+        const int k = k0 + kk, m = m0 + mm, n = n0 + mm;
+        float av = 0.f, bv = 0.f;
+        if (k < Kd && m < M) {
+          if (STAGE == KS_T) av = L.B[((int64_t)rx * N1 + k) * K1 + m];                       // B_r[n1, k1]
+          else if (STAGE == KS_G) av = Tb[((int64_t)rx * K1 + m) * N2 + k];                  // T_r[k1, n2]
+          else if (STAGE == KS_U) av = L.B[((int64_t)rx * N1 + m) * K1 + k];                 // B_r[n1, k1]
+          else av = Tb[((int64_t)rx * N1 + m) * K2 + k];                                     // U_r[n1, k2]
+        }
+        if (k < Kd && n < Nc) {
+          if (STAGE == KS_T) bv = (float)a.Rho[(int64_t)b * a.ldN + (int64_t)k * N2 + n];    // P[n1, n2]
+          else if (STAGE == KS_G) bv = L.C[((int64_t)rx * N2 + k) * K2 + n];                 // C_r[n2, k2]
+          else if (STAGE == KS_U) bv = a.Xd[(int64_t)b * a.K + (int64_t)k * K2 + n];         // X[k1, k2]
+          else bv = L.C[((int64_t)rx * N2 + n) * K2 + k];                                    // C_r[n2, k2]^T
+        }
+        sA[kk][mm] = av;
+        sB[kk][mm] = bv;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          av[i] = sA[kk][ty * 4 + i];
+          bv[i] = sB[kk][tx * 4 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[i][q] = __fmaf_rn(av[i], bv[q], acc[i][q]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + q;
+      if (m >= M || n >= Nc) continue;
+      if (STAGE == KS_T) Tb[((int64_t)r * K1 + m) * N2 + n] = acc[i][q];
+      else if (STAGE == KS_G) {
+        const int64_t j = (int64_t)m * K2 + n;
+        a.Gfull[(int64_t)b * a.K + j] = __fmul_rn(acc[i][q], L.dscale[j]);
+      } else if (STAGE == KS_U) Tb[((int64_t)r * N1 + m) * K2 + n] = acc[i][q];
+      else a.AZ[(int64_t)b * a.ldN + (int64_t)m * N2 + n] = acc[i][q];
+    }
+}
+
+// X_b = reshape(d * z_b) for the Kronecker residual (dense scatter of the nonzero list).
+template <typename VT>
+__global__ void k_kron_scatter(PassArgs<VT> a) {
+  const int b = blockIdx.y;
+  const SigState& s = a.st[b];
+  if (s.done || a.dd.lv[s.level].kind != LK_KRON) return;
+  const LevelDev& L = a.dd.lv[s.level];
+  float* xd = a.Xd + (int64_t)b * a.K;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.K; j += (int64_t)gridDim.x * blockDim.x)
+    xd[j] = 0.f;
+  __syncthreads();
+  // ordering: the zero fill of this block must precede the writes of every block; use one block
+  if (blockIdx.x == 0) {
+    for (int q = threadIdx.x; q < s.n_nz; q += blockDim.x) {
+      const int32_t j = a.nz_idx[(int64_t)b * a.K + q];
+      xd[j] = __fmul_rn((float)a.nz_val[(int64_t)b * a.K + q], L.dscale[j]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ certificate and outputs
+
+// Full-dictionary certificate (a final pass over every atom with the most precise level):
+// gap of the returned point with the stable scaling over all K atoms.
+template <typename VT>
+__global__ void k_cert_finish(PassArgs<VT> a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.sp.B) return;
+  SigState& s = a.st[b];
+  if (s.status != LASSO_OK || s.n_kept == 0 || s.iters == 0) return;
+  const LevelDev& L = a.dd.lv[a.dd.n_levels - 1];
+  double rr = 0.0, yr = 0.0, m1 = 0.0;
+  for (int q = 0; q < a.nrb; ++q) {
+    rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
+    yr += a.part_res[((int64_t)b * a.nrb + q) * 2 + 1];
+  }
+  const int nch = (int)((a.K + CORR_CHUNK - 1) / CORR_CHUNK);
+  for (int c = 0; c < nch; ++c) m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
+  const double lam = s.lam, nrho = sqrt(rr);
+  const double e = s.sum_epsz + residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8);
+  double sp_ = 0.0;
+  if (rr > 0.0) {
+    const double beta = yr / (lam * rr);
+    sp_ = m1 > 0.0 ? fmin(fmax(beta, -1.0 / m1), 1.0 / m1) : beta;
+  }
+  const double P = 0.5 * rr + lam * s.l1;
+  const double D = lam * sp_ * yr - 0.5 * lam * lam * sp_ * sp_ * rr;
+  const double g = fmax(P - D + nrho * e + 0.5 * e * e, 0.0) / s.yy;
+  s.gap = fmax(g, s.gap);
+  if (s.gap > a.sp.tol) s.status = LASSO_WARN_AUDIT;
+}
+
+template <typename VT>
+__global__ void k_outputs(PassArgs<VT> a, float* __restrict__ Xf, double* __restrict__ gaps, int32_t* __restrict__ status,
+                          int32_t* __restrict__ iters) {
+  const int b = blockIdx.y;
+  const SigState& s = a.st[b];
+  if (Xf) {
+    const VT* xo = a.Xout + (int64_t)b * a.K;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.K; j += (int64_t)gridDim.x * blockDim.x)
+      Xf[(int64_t)b * a.K + j] = (float)xo[j];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (gaps) gaps[b] = s.gap;
+    if (status) status[b] = s.status;
+    if (iters) iters[b] = s.iters;
+  }
+}
+
+template <typename VT>
+__global__ void k_load_y(PassArgs<VT> a, const float* __restrict__ Yf, const double* __restrict__ Yd) {
+  const int b = blockIdx.y;
+  VT* y = const_cast<VT*>(a.Yw) + (int64_t)b * a.ldN;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < a.ldN; n += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (n < a.dd.N) v = Yf ? (double)Yf[(int64_t)b * a.dd.N + n] : Yd[(int64_t)b * a.dd.N + n];
+    y[n] = (VT)v;
+  }
+}
+
+// ------------------------------------------------------------------ host driver
+
+int g_num_sms = 0;
+
+static int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 132;
+  }
+  return g_num_sms;
+}
+
+struct SolveIO {
+  const float* Yf = nullptr;      // device, B x N
+  const double* Yd = nullptr;     // device, B x N
+  const double* lambdas = nullptr;  // device
+  int64_t B = 0;
+  double tol = 1e-6;
+  lasso_opts opts;
+  float* Xf = nullptr;            // device outputs (batch API)
+  double* gaps = nullptr;
+  int32_t* status = nullptr;
+  int32_t* iters = nullptr;
+  cudaStream_t stream = nullptr;
+};
+
+// Events of one pass (profile mode): before residual stage, before correlation, before
+// screening, before schedule, end; Kronecker stages are timed between their own events.
+constexpr int PASS_EVENTS = 7;
+
+template <typename VT>
+static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, int corr_grid, size_t corr_smem,
+                        cudaEvent_t* ev) {
+  const int B = pa.sp.B;
+  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+  if (has_kron) {
+    // structured residual: X = d * z, U_r = B_r X, A~z = sum_r U_r C_r^T
+    const int Rmax = [&] {
+      int m = 0;
+      for (int l = 0; l < pa.dd.n_levels; ++l)
+        if (pa.dd.lv[l].kind == LK_KRON) m = std::max(m, pa.dd.lv[l].R);
+      return m;
+    }();
+    const LevelDev* KL = nullptr;
+    for (int l = 0; l < pa.dd.n_levels; ++l)
+      if (pa.dd.lv[l].kind == LK_KRON) KL = &pa.dd.lv[l];
+    const int N1 = KL->N1, N2 = KL->N2, K2 = KL->K2;
+    auto tiles = [](int v) { return (unsigned)((v + GEMM_T - 1) / GEMM_T); };
+    k_kron_scatter<VT><<<dim3(1, B), 256, 0, st>>>(pa);
+    k_kron_gemm<VT, KS_U><<<dim3(tiles(K2), tiles(N1), B * Rmax), 256, 0, st>>>(pa);
+    k_kron_gemm<VT, KS_Y><<<dim3(tiles(N2), tiles(N1), B), 256, 0, st>>>(pa);
+  }
+  if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+  k_residual<VT><<<dim3(pa.nrb, B), RES_THREADS, 0, st>>>(pa);
+  if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
+  if (has_kron) {
+    const int Rmax = [&] {
+      int m = 0;
+      for (int l = 0; l < pa.dd.n_levels; ++l)
+        if (pa.dd.lv[l].kind == LK_KRON) m = std::max(m, pa.dd.lv[l].R);
+      return m;
+    }();
+    const LevelDev* KL = nullptr;
+    for (int l = 0; l < pa.dd.n_levels; ++l)
+      if (pa.dd.lv[l].kind == LK_KRON) KL = &pa.dd.lv[l];
+    const int K1 = KL->K1, N2 = KL->N2, K2 = KL->K2;
+    auto tiles = [](int v) { return (unsigned)((v + GEMM_T - 1) / GEMM_T); };
+    k_kron_gemm<VT, KS_T><<<dim3(tiles(N2), tiles(K1), B * Rmax), 256, 0, st>>>(pa);
+    k_kron_gemm<VT, KS_G><<<dim3(tiles(K2), tiles(K1), B), 256, 0, st>>>(pa);
+  }
+  if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+  k_corr<VT, CORR_PASS><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
+  if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
+  k_screen<VT><<<B, SCREEN_THREADS, 0, st>>>(pa);
+  if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
+  k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+  if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
+}
+
+static int pass_launches(bool has_kron) { return has_kron ? 9 : 4; }
+
+template <typename VT>
+static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats* stats) {
+  auto t_start = std::chrono::steady_clock::now();
+  const lasso_opts& o = io.opts;
+  const int64_t B = io.B;
+  cudaStream_t st = io.stream ? io.stream : w->stream;
+  if (!io.stream) LASSO_CUDA_TRY(cudaStreamSynchronize(0));   // inputs written on the legacy stream
+  PassArgs<VT> pa;
+  memset(&pa, 0, sizeof(pa));
+  std::vector<const HostLevel*> order;
+  int rc = build_dict_dev(d, o.final_fp64 != 0, &pa.dd, &order);
+  if (rc) return rc;
+  bool has_kron = false;
+  int rmax = 0;
+  for (int l = 0; l < pa.dd.n_levels; ++l) {
+    has_kron |= pa.dd.lv[l].kind == LK_KRON;
+    if (pa.dd.lv[l].kind == LK_KRON) rmax = std::max(rmax, pa.dd.lv[l].R);
+  }
+  if (has_kron && B * rmax > 65535) return LASSO_ERR_UNSUPPORTED;
+  pa.sp.tol = io.tol;
+  pa.sp.Gamma = o.Gamma;
+  pa.sp.tau = o.tau;
+  pa.sp.L = d->L;
+  pa.sp.algo = o.algo;
+  pa.sp.rule = o.rule;
+  pa.sp.screen_every = std::max(1, o.screen_every);
+  pa.sp.max_iter = std::max(1, o.max_iter);
+  pa.sp.B = (int)B;
+  pa.Yw = (const VT*)w->Yw;
+  pa.Rho = (VT*)w->Rho;
+  pa.X = (VT*)w->X;
+  pa.Z = (VT*)w->Z;
+  pa.G = (VT*)w->G;
+  pa.Xout = (VT*)w->Xout;
+  pa.nz_val = (VT*)w->nz_val;
+  pa.nz_idx = w->nz_idx;
+  pa.kept = w->kept;
+  pa.c0ub = w->c0ub;
+  pa.part_res = w->part_res;
+  pa.part_corr = w->part_corr;
+  pa.offsets = w->offsets;
+  pa.counters = w->counters;
+  pa.alg_bytes = w->alg_bytes;
+  pa.st = w->st;
+  pa.Gfull = w->Gfull;
+  pa.AZ = w->AZ;
+  pa.Xd = w->Xd;
+  pa.Tk = w->Tk;
+  pa.K = d->K;
+  pa.ldN = d->ldN;
+  pa.nrb = w->nrb;
+  pa.nch = w->nch;
+  const size_t vs = sizeof(VT);
+  const size_t BK = (size_t)B * d->K;
+  LASSO_CUDA_TRY(cudaMemsetAsync(w->X, 0, BK * vs, st));
+  LASSO_CUDA_TRY(cudaMemsetAsync(w->Z, 0, BK * vs, st));
+  LASSO_CUDA_TRY(cudaMemsetAsync(w->Xout, 0, BK * vs, st));
+  LASSO_CUDA_TRY(cudaMemsetAsync(w->Rho, 0, (size_t)B * d->ldN * vs, st));
+  LASSO_CUDA_TRY(cudaMemsetAsync(w->part_res, 0, (size_t)B * w->nrb * 16, st));
+  k_load_y<VT><<<dim3((unsigned)((d->ldN + 255) / 256), (unsigned)B), 256, 0, st>>>(pa, io.Yf, io.Yd);
+  k_init_state<VT><<<(unsigned)B, 256, 0, st>>>(pa, io.lambdas);
+  // smem for the staged vector
+  size_t corr_smem = (size_t)d->ldN * 8;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[vs == 8]) {
+    cudaFuncSetAttribute(k_corr<VT, CORR_PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_corr<VT, CORR_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_corr<VT, CORR_CERT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set[vs == 8] = true;
+  }
+  const int corr_grid = num_sms() * 8;
+  // init: lambda_max and a^T y bounds with the most precise level
+  k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+  k_corr<VT, CORR_INIT><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
+  k_init_finish<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa, o.lambda_relative);
+  k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+  LASSO_CUDA_TRY(cudaGetLastError());
+  LASSO_CUDA_TRY(cudaMemsetAsync(w->alg_bytes, 0, 16 * sizeof(double), st));
+  // capture k passes
+  const int k = std::max(1, o.passes_per_sync);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  LASSO_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  std::vector<cudaEvent_t> evs;
+  if (o.profile) {
+    evs.resize((size_t)k * PASS_EVENTS);
+    for (auto& e : evs) LASSO_CUDA_TRY(cudaEventCreate(&e));
+  }
+  double kms[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < k; ++i)
+    launch_pass<VT>(pa, st, has_kron, corr_grid, corr_smem, o.profile ? &evs[(size_t)i * PASS_EVENTS] : nullptr);
+  cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  if (ce != cudaSuccess) {
+    set_last_error(cudaGetErrorString(ce), __FILE__, __LINE__);
+    return LASSO_ERR_CUDA;
+  }
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    set_last_error(cudaGetErrorString(ce), __FILE__, __LINE__);
+    return LASSO_ERR_CUDA;
+  }
+  int64_t replays = 0;
+  int result = LASSO_OK;
+  const int64_t max_replays = (int64_t)pa.sp.max_iter / k + 2;
+  while (true) {
+    ce = cudaMemcpyAsync(w->h_counters, w->counters, 4, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+      set_last_error(cudaGetErrorString(ce), __FILE__, __LINE__);
+      result = LASSO_ERR_CUDA;
+      break;
+    }
+    if (o.profile && replays > 0) {
+      for (int i = 0; i < k; ++i) {
+        cudaEvent_t* e = &evs[(size_t)i * PASS_EVENTS];
+        float t;
+        if (cudaEventElapsedTime(&t, e[0], e[1]) == cudaSuccess) kms[4] += t;
+        if (cudaEventElapsedTime(&t, e[1], e[2]) == cudaSuccess) kms[0] += t;
+        if (cudaEventElapsedTime(&t, e[2], e[3]) == cudaSuccess) kms[4] += t;
+        if (cudaEventElapsedTime(&t, e[3], e[4]) == cudaSuccess) kms[1] += t;
+        if (cudaEventElapsedTime(&t, e[4], e[5]) == cudaSuccess) kms[2] += t;
+        if (cudaEventElapsedTime(&t, e[5], e[6]) == cudaSuccess) kms[3] += t;
+      }
+      cudaGetLastError();   // a failed timing query must not leave a sticky error behind
+    }
+    if (w->h_counters[0] >= B) break;
+    if (replays >= max_replays) break;
+    if (o.time_limit_s > 0.0) {
+      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+      if (el > o.time_limit_s) {
+        result = LASSO_ERR_TIMEOUT;
+        break;
+      }
+    }
+    ce = cudaGraphLaunch(exec, st);
+    if (ce != cudaSuccess) {
+      set_last_error(cudaGetErrorString(ce), __FILE__, __LINE__);
+      result = LASSO_ERR_CUDA;
+      break;
+    }
+    ++replays;
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  for (auto& e : evs) cudaEventDestroy(e);
+  if (result == LASSO_ERR_CUDA) return result;
+  double hbytes[16] = {0};
+  LASSO_CUDA_TRY(cudaMemcpyAsync(hbytes, w->alg_bytes, sizeof(hbytes), cudaMemcpyDeviceToHost, st));
+  LASSO_CUDA_TRY(cudaStreamSynchronize(st));
+  int64_t launches = 6 + replays * (int64_t)k * pass_launches(has_kron);
+  if (o.certify_full && result == LASSO_OK) {
+    // certificate over every atom (offsets: K / CHUNK items per signal)
+    std::vector<int32_t> offs(B + 1);
+    const int nch = (int)((d->K + CORR_CHUNK - 1) / CORR_CHUNK);
+    for (int64_t b = 0; b <= B; ++b) offs[b] = (int32_t)(b * nch);
+    LASSO_CUDA_TRY(cudaMemcpyAsync(w->offsets, offs.data(), (B + 1) * 4, cudaMemcpyHostToDevice, st));
+    k_corr<VT, CORR_CERT><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
+    k_cert_finish<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa);
+    LASSO_CUDA_TRY(cudaStreamSynchronize(st));
+    launches += 2;
+  }
+  launches += 1;
+  k_outputs<VT><<<dim3(io.Xf ? 64 : 1, (unsigned)B), 256, 0, st>>>(pa, io.Xf, io.gaps, io.status, io.iters);
+  LASSO_CUDA_TRY(cudaGetLastError());
+  LASSO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (stats) {
+    std::vector<SigState> hs(B);
+    LASSO_CUDA_TRY(cudaMemcpy(hs.data(), w->st, B * sizeof(SigState), cudaMemcpyDeviceToHost));
+    memset(stats, 0, sizeof(*stats));
+    for (int64_t b = 0; b < B; ++b) {
+      stats->passes = std::max<int64_t>(stats->passes, hs[b].iters);
+      for (int l = 0; l < MAX_LEVELS; ++l) stats->level_passes[l] += hs[b].level_passes[l];
+      stats->kept_final += hs[b].n_kept;
+    }
+    stats->lambda_max = hs[0].lam_max_lb;
+    stats->lambda = hs[0].lam;
+    stats->launches = launches;
+    const int per_pass[6] = {1, 1, 1, 1, has_kron ? 5 : 0, 0};
+    for (int q = 0; q < 6; ++q) {
+      stats->kernel_launches[q] = replays * (int64_t)k * per_pass[q];
+      stats->kernel_ms[q] = kms[q];
+      stats->kernel_bytes[q] = hbytes[q];
+    }
+    for (int l = 0; l < MAX_LEVELS; ++l) stats->level_atoms[l] = hbytes[8 + l];
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  return result;
+}
+
+}  // namespace lasso
+
+using namespace lasso;
+
+void lasso_workspace_free(lasso::Workspace* ws) { free_ws(ws); }
+
+extern "C" void lasso_opts_default(lasso_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->Gamma = 0.5;
+  o->algo = LASSO_FISTA;
+  o->rule = LASSO_RULE_GAP;
+  o->screen_every = 1;
+  o->max_iter = 100000;
+  o->lambda_relative = 0;
+  o->final_fp64 = 0;
+  o->certify_full = 1;
+  o->passes_per_sync = 8;
+  o->tensor_cores = 1;
+  o->tau = 1e-9;
+  o->time_limit_s = 0.0;
+  o->profile = 0;
+}
+
+static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
+  if (!d || io.B <= 0 || !(io.tol > 0.0)) return LASSO_ERR_INVALID_ARG;
+  if (d->ldN > 24576) return LASSO_ERR_UNSUPPORTED;
+  if (!d->prepared) {
+    int rc = dict_prepare(d, 0.0);
+    if (rc) return rc;
+  }
+  const bool vt_double = d->exact_kind == LK_F64 || io.opts.final_fp64;
+  Workspace* w = nullptr;
+  int rc = get_ws(d, io.B, vt_double, &w);
+  if (rc) return rc;
+  if (vt_double) return run_solve<double>(d, w, io, stats);
+  return run_solve<float>(d, w, io, stats);
+}
+
+extern "C" int lasso_solve_batch(lasso_dict* d, const float* d_Y, const double* d_lambdas, int64_t B, double tol,
+                                 const lasso_opts* opts, float* d_X, double* d_gaps, int32_t* d_status,
+                                 int32_t* d_iters, void* stream, lasso_stats* stats) {
+  if (!d_Y || !d_lambdas || !d_X) return LASSO_ERR_INVALID_ARG;
+  SolveIO io;
+  io.Yf = d_Y;
+  io.lambdas = d_lambdas;
+  io.B = B;
+  io.tol = tol;
+  if (opts) io.opts = *opts;
+  else lasso_opts_default(&io.opts);
+  io.Xf = d_X;
+  io.gaps = d_gaps;
+  io.status = d_status;
+  io.iters = d_iters;
+  io.stream = (cudaStream_t)stream;
+  return solve_common(d, io, stats);
+}
+
+extern "C" int lasso_solve_batch_host(lasso_dict* d, const float* Y, const double* lambdas, int64_t B, double tol,
+                                      const lasso_opts* opts, float* X, double* gaps, int32_t* status,
+                                      lasso_stats* stats) {
+  if (!d || !Y || !lambdas || !X || B <= 0) return LASSO_ERR_INVALID_ARG;
+  float *dY = nullptr, *dX = nullptr;
+  double *dl = nullptr, *dg = nullptr;
+  int32_t* ds = nullptr;
+  const size_t BN = (size_t)B * d->N, BK = (size_t)B * d->K;
+  int rc = LASSO_OK;
+  if (cudaMalloc(&dY, BN * 4) != cudaSuccess || cudaMalloc(&dX, BK * 4) != cudaSuccess ||
+      cudaMalloc(&dl, B * 8) != cudaSuccess || cudaMalloc(&dg, B * 8) != cudaSuccess ||
+      cudaMalloc(&ds, B * 4) != cudaSuccess) {
+    rc = LASSO_ERR_NOMEM;
+  }
+  if (!rc && (cudaMemcpy(dY, Y, BN * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+              cudaMemcpy(dl, lambdas, B * 8, cudaMemcpyHostToDevice) != cudaSuccess))
+    rc = LASSO_ERR_CUDA;
+  if (!rc) rc = lasso_solve_batch(d, dY, dl, B, tol, opts, dX, dg, ds, nullptr, nullptr, stats);
+  if (rc == LASSO_OK || rc == LASSO_ERR_MAXITER || rc == LASSO_ERR_TIMEOUT) {
+    if (cudaMemcpy(X, dX, BK * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (gaps && cudaMemcpy(gaps, dg, B * 8, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (status && cudaMemcpy(status, ds, B * 4, cudaMemcpyDeviceToHost) != cudaSuccess))
+      rc = LASSO_ERR_CUDA;
+  }
+  cudaFree(dY);
+  cudaFree(dX);
+  cudaFree(dl);
+  cudaFree(dg);
+  cudaFree(ds);
+  return rc;
+}
+
+extern "C" int lasso_solve(lasso_dict* d, const double* y, double lambda, double tol, const lasso_opts* opts,
+                           double* x, double* gap, int32_t* kept, int64_t* n_kept, lasso_stats* stats) {
+  if (!d || !y || !x) return LASSO_ERR_INVALID_ARG;
+  double *dy = nullptr, *dl = nullptr;
+  if (cudaMalloc(&dy, d->N * 8) != cudaSuccess || cudaMalloc(&dl, 8) != cudaSuccess) {
+    cudaFree(dy);
+    return LASSO_ERR_NOMEM;
+  }
+  cudaMemcpy(dy, y, d->N * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dl, &lambda, 8, cudaMemcpyHostToDevice);
+  SolveIO io;
+  io.Yd = dy;
+  io.lambdas = dl;
+  io.B = 1;
+  io.tol = tol;
+  if (opts) io.opts = *opts;
+  else lasso_opts_default(&io.opts);
+  lasso_stats local;
+  int rc = solve_common(d, io, stats ? stats : &local);
+  cudaFree(dy);
+  cudaFree(dl);
+  if (rc != LASSO_OK && rc != LASSO_ERR_MAXITER && rc != LASSO_ERR_TIMEOUT && rc != LASSO_WARN_AUDIT) return rc;
+  Workspace* w = d->ws;
+  SigState s;
+  if (cudaMemcpy(&s, w->st, sizeof(s), cudaMemcpyDeviceToHost) != cudaSuccess) return LASSO_ERR_CUDA;
+  if (w->vt_double) {
+    if (cudaMemcpy(x, w->Xout, d->K * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return LASSO_ERR_CUDA;
+  } else {
+    std::vector<float> xf(d->K);
+    if (cudaMemcpy(xf.data(), w->Xout, d->K * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return LASSO_ERR_CUDA;
+    for (int64_t j = 0; j < d->K; ++j) x[j] = xf[j];
+  }
+  if (gap) *gap = s.gap;
+  if (n_kept) *n_kept = s.n_kept;
+  if (kept && s.n_kept > 0) {
+    if (cudaMemcpy(kept, w->kept + (int64_t)s.parity * d->K, s.n_kept * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return LASSO_ERR_CUDA;
+  }
+  return s.status != LASSO_OK ? s.status : rc;
+}
+
+template <typename VT>
+__global__ void k_copy_lmax(PassArgs<VT> a, double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < a.sp.B) out[b] = a.st[b].lam_max_lb;
+}
+
+template <typename VT>
+static int run_lambda_max(lasso_dict* d, Workspace* w, const float* Y, int64_t B, double* out, cudaStream_t st) {
+  PassArgs<VT> pa;
+  memset(&pa, 0, sizeof(pa));
+  int rc = build_dict_dev(d, false, &pa.dd, nullptr);
+  if (rc) return rc;
+  pa.sp.B = (int)B;
+  pa.sp.L = 1.0;
+  pa.Yw = (const VT*)w->Yw;
+  pa.Rho = (VT*)w->Rho;
+  pa.kept = w->kept;
+  pa.c0ub = w->c0ub;
+  pa.part_res = w->part_res;
+  pa.part_corr = w->part_corr;
+  pa.offsets = w->offsets;
+  pa.counters = w->counters;
+  pa.st = w->st;
+  pa.X = (VT*)w->X;
+  pa.Z = (VT*)w->Z;
+  pa.G = (VT*)w->G;
+  pa.K = d->K;
+  pa.ldN = d->ldN;
+  pa.nrb = w->nrb;
+  pa.nch = w->nch;
+  double* ones = nullptr;
+  LASSO_CUDA_TRY(cudaMalloc(&ones, B * 8));
+  std::vector<double> h(B, 1.0);
+  cudaMemcpyAsync(ones, h.data(), B * 8, cudaMemcpyHostToDevice, st);
+  k_load_y<VT><<<dim3((unsigned)((d->ldN + 255) / 256), (unsigned)B), 256, 0, st>>>(pa, Y, nullptr);
+  k_init_state<VT><<<(unsigned)B, 256, 0, st>>>(pa, ones);
+  cudaFuncSetAttribute(k_corr<VT, CORR_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+  k_corr<VT, CORR_INIT><<<num_sms() * 8, CORR_THREADS, (size_t)d->ldN * 8, st>>>(pa);
+  k_init_finish<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa, 1);
+  k_copy_lmax<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa, out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(ones);
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
+    return LASSO_ERR_CUDA;
+  }
+  return LASSO_OK;
+}
+
+extern "C" int lasso_lambda_max(lasso_dict* d, const float* d_Y, int64_t B, double* d_out, void* stream) {
+  if (!d || !d_Y || !d_out || B <= 0) return LASSO_ERR_INVALID_ARG;
+  const bool vt_double = d->exact_kind == LK_F64;
+  Workspace* w = nullptr;
+  int rc = get_ws(d, B, vt_double, &w);
+  if (rc) return rc;
+  cudaStream_t st = stream ? (cudaStream_t)stream : w->stream;
+  if (!stream) LASSO_CUDA_TRY(cudaStreamSynchronize(0));
+  if (vt_double) return run_lambda_max<double>(d, w, d_Y, B, d_out, st);
+  return run_lambda_max<float>(d, w, d_Y, B, d_out, st);
+}

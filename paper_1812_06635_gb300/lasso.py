@@ -1,0 +1,255 @@
+"""Python API over the C ABI: dictionaries, single and batched screened Lasso solves, and the
+autograd wrapper.  PyTorch provides device memory and streams only; every step of the solve
+runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native as nat
+
+LEVEL_BF16, LEVEL_FP8, LEVEL_KRON, LEVEL_F32 = 2, 3, 4, 5
+FISTA, ISTA = 0, 1
+RULE_GAP, RULE_DST = 0, 1
+STATUS = {0: "ok", -1: "invalid_arg", -2: "cuda", -3: "nonfinite", -4: "maxiter", -5: "timeout",
+          -6: "unsupported", -7: "nomem", 1: "warn_audit"}
+
+
+def make_opts(**kw) -> nat.LassoOpts:
+    """lasso_opts with the library defaults, overridden by keyword (same field names)."""
+    o = nat.LassoOpts()
+    nat.load().lasso_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Stats:
+    passes: int
+    level_passes: list
+    kept_final: int
+    lambda_max: float
+    lam: float
+    seconds: float
+    launches: int = 0
+    kernel_launches: list = None
+    kernel_ms: list = None
+    kernel_bytes: list = None
+    level_atoms: list = None
+
+    KINDS = ("residual", "corr", "screen", "schedule", "kron", "tc_gemm")
+
+    @staticmethod
+    def of(s: nat.LassoStats) -> "Stats":
+        return Stats(int(s.passes), [int(v) for v in s.level_passes], int(s.kept_final), float(s.lambda_max),
+                     float(s.lambda_), float(s.seconds), int(s.launches), [int(v) for v in s.kernel_launches],
+                     [float(v) for v in s.kernel_ms], [float(v) for v in s.kernel_bytes],
+                     [float(v) for v in s.level_atoms])
+
+
+def _ptr(a) -> C.c_void_p:
+    if a is None:
+        return C.c_void_p(0)
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+class Dictionary:
+    """A dictionary (exact A) and its ladder of approximations, owned by the library."""
+
+    def __init__(self, handle: C.c_void_p, N: int, K: int):
+        self._h = handle
+        self.N, self.K = N, K
+
+    # ------------------------------------------------------------ construction
+    @classmethod
+    def dense(cls, A, dtype: str = "f32", normalize: bool = False, atom_major: bool = False) -> "Dictionary":
+        """A: host array, N x K with atoms as columns (or K x N rows = atoms if atom_major)."""
+        lib = nat.load()
+        npdt = np.float64 if dtype == "f64" else np.float32
+        if hasattr(A, "detach"):
+            A = A.detach().cpu().numpy()
+        A = np.asarray(A, dtype=npdt)
+        if atom_major:
+            K, N = A.shape
+            arr = np.ascontiguousarray(A)
+            ld, am = N, 1
+        else:
+            N, K = A.shape
+            arr = np.ascontiguousarray(A.T)   # atom-major copy (row j = atom j)
+            ld, am = N, 1
+        h = C.c_void_p()
+        nat.check(lib.lasso_dict_create_dense(_ptr(arr), 0 if dtype == "f64" else 1, N, K, ld, am, int(normalize), 1,
+                                              C.byref(h)), "lasso_dict_create_dense")
+        return cls(h, N, K)
+
+    @classmethod
+    def kron(cls, Bf, Cf) -> "Dictionary":
+        """A = (sum_r B_r (x) C_r) diag(d), unit atoms; Bf: R x N1 x K1, Cf: R x N2 x K2."""
+        lib = nat.load()
+        Bf = np.ascontiguousarray(np.asarray(Bf, dtype=np.float32))
+        Cf = np.ascontiguousarray(np.asarray(Cf, dtype=np.float32))
+        R, N1, K1 = Bf.shape
+        _, N2, K2 = Cf.shape
+        h = C.c_void_p()
+        nat.check(lib.lasso_dict_create_kron(_ptr(Bf), _ptr(Cf), R, N1, K1, N2, K2, 1, C.byref(h)),
+                  "lasso_dict_create_kron")
+        return cls(h, N1 * N2, K1 * K2)
+
+    def add_level(self, kind: int, param: int = 0) -> "Dictionary":
+        nat.check(nat.load().lasso_dict_add_level(self._h, kind, param), "lasso_dict_add_level")
+        return self
+
+    def set_rc(self, level: int, rc: float) -> "Dictionary":
+        nat.check(nat.load().lasso_dict_set_rc(self._h, level, rc), "lasso_dict_set_rc")
+        return self
+
+    def prepare(self, L: float = 0.0) -> "Dictionary":
+        nat.check(nat.load().lasso_dict_prepare(self._h, float(L)), "lasso_dict_prepare")
+        return self
+
+    def info(self) -> dict:
+        inf = nat.LassoDictInfo()
+        nat.check(nat.load().lasso_dict_info(self._h, C.byref(inf)), "lasso_dict_info")
+        n = inf.n_levels
+        return {"N": inf.N, "K": inf.K, "n_levels": n, "L": inf.L, "kind": list(inf.kind[:n]),
+                "rc": list(inf.rc[:n]), "eps_mean": list(inf.eps_mean[:n]), "eps_max": list(inf.eps_max[:n])}
+
+    def level_data(self, level: int, atoms: bool = True):
+        """(eps (K,), dequantised atoms (K x N, row j = atom j) or None) of a level, as FP64."""
+        eps = np.zeros(self.K)
+        at = np.zeros((self.K, self.N)) if atoms else None
+        nat.check(nat.load().lasso_dict_level_host(self._h, level, _ptr(eps), _ptr(at)), "lasso_dict_level_host")
+        return eps, at
+
+    def close(self):
+        if self._h:
+            nat.load().lasso_dict_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ solves
+    def solve(self, y, lam: float, tol: float = 1e-6, **opts):
+        """One signal, host buffers.  Returns (x, rel_gap, kept, Stats); status errors raise."""
+        lib = nat.load()
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+        x = np.zeros(self.K)
+        kept = np.zeros(self.K, dtype=np.int32)
+        gap = C.c_double()
+        nk = C.c_int64()
+        st = nat.LassoStats()
+        o = make_opts(**opts)
+        code = lib.lasso_solve(self._h, _ptr(y), float(lam), float(tol), C.byref(o), _ptr(x), C.byref(gap),
+                               _ptr(kept), C.byref(nk), C.byref(st))
+        nat.check(code, "lasso_solve", ok=(0, 1))
+        return x, gap.value, kept[: nk.value].copy(), Stats.of(st)
+
+    def solve_batch(self, Y, lambdas, tol: float = 1e-6, stream=None, **opts):
+        """Batch on the device.  Y: torch CUDA float32 (B x N); lambdas: torch CUDA float64 (B,).
+
+        Returns (X (B x K float32), gaps (B float64), status (B int32), iters (B int32), Stats).
+        """
+        import torch
+        lib = nat.load()
+        assert Y.is_cuda and Y.dtype == torch.float32 and Y.is_contiguous()
+        B = Y.shape[0]
+        lam = lambdas.to(device=Y.device, dtype=torch.float64).contiguous()
+        X = torch.empty((B, self.K), dtype=torch.float32, device=Y.device)
+        gaps = torch.empty(B, dtype=torch.float64, device=Y.device)
+        status = torch.empty(B, dtype=torch.int32, device=Y.device)
+        iters = torch.empty(B, dtype=torch.int32, device=Y.device)
+        st = nat.LassoStats()
+        o = make_opts(**opts)
+        s = stream if stream is not None else torch.cuda.current_stream(Y.device)
+        code = lib.lasso_solve_batch(self._h, _ptr(Y), _ptr(lam), B, float(tol), C.byref(o), _ptr(X), _ptr(gaps),
+                                     _ptr(status), _ptr(iters), C.c_void_p(s.cuda_stream), C.byref(st))
+        nat.check(code, "lasso_solve_batch", ok=(0, -4, -5))
+        return X, gaps, status, iters, Stats.of(st)
+
+    def solve_batch_host(self, Y, lambdas, tol: float = 1e-6, **opts):
+        """Batch with host buffers (the library copies in and out)."""
+        lib = nat.load()
+        Y = np.ascontiguousarray(np.asarray(Y, dtype=np.float32))
+        lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+        B = Y.shape[0]
+        X = np.zeros((B, self.K), dtype=np.float32)
+        gaps = np.zeros(B)
+        status = np.zeros(B, dtype=np.int32)
+        st = nat.LassoStats()
+        o = make_opts(**opts)
+        code = lib.lasso_solve_batch_host(self._h, _ptr(Y), _ptr(lam), B, float(tol), C.byref(o), _ptr(X),
+                                          _ptr(gaps), _ptr(status), C.byref(st))
+        nat.check(code, "lasso_solve_batch_host", ok=(0, -4, -5))
+        return X, gaps, status, Stats.of(st)
+
+    def lambda_max(self, Y):
+        import torch
+        B = Y.shape[0]
+        out = torch.empty(B, dtype=torch.float64, device=Y.device)
+        s = torch.cuda.current_stream(Y.device)
+        nat.check(nat.load().lasso_lambda_max(self._h, _ptr(Y), B, _ptr(out), C.c_void_p(s.cuda_stream)),
+                  "lasso_lambda_max")
+        return out
+
+    def backward(self, Y, X, G, want_dA: bool = True):
+        """(dL/dY (B x N), dL/dA (K x N atom-major, summed over the batch) or None) for dL/dX = G."""
+        import torch
+        B = Y.shape[0]
+        dY = torch.empty_like(Y)
+        dA = torch.zeros((self.K, self.N), dtype=torch.float32, device=Y.device) if want_dA else None
+        s = torch.cuda.current_stream(Y.device)
+        nat.check(nat.load().lasso_backward(self._h, _ptr(Y), _ptr(X.contiguous()), _ptr(G.contiguous()), B, _ptr(dY),
+                                            _ptr(dA), C.c_void_p(s.cuda_stream)), "lasso_backward")
+        return dY, dA
+
+
+def _autograd():
+    import torch
+
+    class LassoFn(torch.autograd.Function):
+        """x* = argmin 1/2||A x - y||^2 + lam ||x||_1 per row of Y, differentiable in Y and A.
+
+        Forward: ``Dictionary.solve_batch``; backward: the support-system adjoint (lambda fixed).
+        ``A`` is the dense N x K tensor the dictionary was built from (its gradient is returned
+        as N x K); pass None to skip dL/dA.
+        """
+
+        @staticmethod
+        def forward(ctx, Y, A, dictionary, lambdas, tol, opts):
+            X, gaps, status, iters, _ = dictionary.solve_batch(Y.contiguous(), lambdas, tol, **(opts or {}))
+            ctx.dictionary = dictionary
+            ctx.want_dA = A is not None and A.requires_grad
+            ctx.save_for_backward(Y, X)
+            return X
+
+        @staticmethod
+        def backward(ctx, gX):
+            Y, X = ctx.saved_tensors
+            dY, dA = ctx.dictionary.backward(Y.contiguous(), X, gX.contiguous().float(), want_dA=ctx.want_dA)
+            return dY, (dA.t().contiguous() if dA is not None else None), None, None, None, None
+
+    return LassoFn
+
+
+class _LazyFn:
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyFn._fn is None:
+            _LazyFn._fn = _autograd()
+        return _LazyFn._fn.apply(*args)
+
+
+LassoFn = _LazyFn()

@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads without a GPU and exports every function include/lasso.h declares."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lasso.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lasso_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1812_06635_gb300 import build, _native
+    build.build()
+    return _native.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    from paper_1812_06635_gb300 import _native
+    assert sorted(n for n, _, _ in _native.SIGNATURES) == _declared()
+
+
+def test_host_only_calls(lib):
+    from paper_1812_06635_gb300 import _native
+    o = _native.LassoOpts()
+    lib.lasso_opts_default(C.byref(o))
+    assert o.Gamma == 0.5 and o.screen_every == 1 and o.certify_full == 1 and o.passes_per_sync == 8
+    assert lib.lasso_strerror(-4).decode().startswith("iteration limit")
+    assert b"sm_103a" in lib.lasso_build_info()
+    # argument validation happens before any device call
+    h = C.c_void_p()
+    assert lib.lasso_dict_create_dense(None, 1, 10, 10, 10, 1, 0, 1, C.byref(h)) == -1
+    assert lib.lasso_dict_create_kron(None, None, 1, 2, 2, 2, 2, 1, C.byref(h)) == -1
+    assert lib.lasso_dict_add_level(None, 2, 0) == -1
+    assert lib.lasso_solve(None, None, 1.0, 1e-6, None, None, None, None, None, None) == -1
+
+
+def test_library_is_built_for_sm_103a_only():
+    from paper_1812_06635_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
