@@ -172,6 +172,20 @@ int lasso_solve_batch_host(lasso_dict* dict, const float* Y_host, const double* 
 /* lambda_max = ||A^T y||_inf of B signals (device buffers, exact level, FP64 output). */
 int lasso_lambda_max(lasso_dict* dict, const float* d_Y, int64_t B, double* d_out, void* stream);
 
+/* Same values as lasso_lambda_max, for callers that cannot allocate device memory (their
+ * device memory belongs to another allocator, or they cannot afford cudaMalloc's implicit
+ * synchronisation).  The paper has no counterpart: this is a deployment variant.
+ * It allocates nothing: its scratch is a fixed 8 MiB array inside the library (1048576
+ * doubles, held by every GPU that loads the library until the process exits), so it needs
+ * B * ceil(K / 256) <= 1048576 and B <= 65535, else it returns LASSO_ERR_UNSUPPORTED.
+ * Device buffers: d_Y (B x N FP32), d_out (B FP64).  The work is queued on `stream` (a
+ * cudaStream_t; the call does not wait for it).  The first call on each device looks up the
+ * scratch address with that device current; make that first call before any stream capture.
+ * Every call shares the one scratch array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. */
+int lasso_lambda_max_noalloc(const lasso_dict* dict, const float* d_Y, int64_t B, double* d_out,
+                             void* stream);
+
 /* Derivative of L(x*(y, A)) through the support system (not in the paper; derived from the
  * KKT conditions of Section II): with S = supp(x_b), u = (A_S^T A_S)^{-1} g_S,
  * dL/dy_b = A_S u and dL/dA[:, S] += r u^T - (A_S u) x_S^T, r = y_b - A_S x_S.  lambda is held

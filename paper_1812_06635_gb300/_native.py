@@ -83,6 +83,7 @@ SIGNATURES = [
     ("lasso_solve_batch_host", C.c_int, [P, P, P, I64, C.c_double, C.POINTER(LassoOpts), P, P, P,
                                          C.POINTER(LassoStats)]),
     ("lasso_lambda_max", C.c_int, [P, P, I64, P, P]),
+    ("lasso_lambda_max_noalloc", C.c_int, [P, P, I64, P, P]),
     ("lasso_backward", C.c_int, [P, P, P, P, I64, P, P, P]),
     ("lasso_strerror", C.c_char_p, [C.c_int]),
     ("lasso_build_info", C.c_char_p, []),

@@ -203,6 +203,17 @@ class Dictionary:
                   "lasso_lambda_max")
         return out
 
+    def lambda_max_noalloc(self, Y, out=None):
+        """lambda_max through the allocation-free entry point; ``out`` (B float64) may be given."""
+        import torch
+        B = Y.shape[0]
+        if out is None:
+            out = torch.empty(B, dtype=torch.float64, device=Y.device)
+        s = torch.cuda.current_stream(Y.device)
+        nat.check(nat.load().lasso_lambda_max_noalloc(self._h, _ptr(Y), B, _ptr(out), C.c_void_p(s.cuda_stream)),
+                  "lasso_lambda_max_noalloc")
+        return out
+
     def backward(self, Y, X, G, want_dA: bool = True):
         """(dL/dY (B x N), dL/dA (K x N atom-major, summed over the batch) or None) for dL/dX = G."""
         import torch
