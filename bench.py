@@ -63,7 +63,8 @@ def _workload_config(B):
     return {"workload": f"c3 batched mixed precision: dense 2048x8192 FP32 dictionary (unit atoms), {B} signals "
                         "per GPU, x0 Bernoulli(p_i) p_i~U[0.01,0.05], lambda_i/lambda_max~U[0.1,0.9], rel gap 1e-6",
             "N": 2048, "K": 8192, "signals_per_gpu": B, "ladder": ["fp8_e4m3_atom_scaled", "bf16", "f32_exact"],
-            "tol": TOL, "certify_full": True, "l2": "flushed between timed steps (512 MB write)"}
+            "tol": TOL, "stopping_certificate": "full-dictionary duality gap bound (rounding folded in)",
+            "l2": "flushed between timed steps (512 MB write)"}
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg

@@ -18,8 +18,9 @@
  *  - Kronecker dictionaries: A = (sum_{r<R} B_r (x) C_r) diag(d) with B_r: N1 x K1 and
  *    C_r: N2 x K2 row-major, N = N1 N2, K = K1 K2, atom k1 K2 + k2, row n1 N2 + n2, and
  *    d_j = 1 / ||(sum_r B_r (x) C_r) e_j||_2 computed by the library in FP64 (unit atoms).
- *  - "Relative gap" is G / ||y||^2 where G is an upper bound of the duality gap of the
- *    returned point for the original problem (rounding of every kernel is folded in).
+ *  - "Relative gap" is G / ||y||^2 where G is an upper bound of the duality gap G(x, theta|A)
+ *    of the returned point for the original problem over the whole dictionary (rounding of
+ *    every kernel is folded in).  A signal stops when this bound is <= tol at the exact level.
  *  - Every call returns a status (lasso_status) and never aborts; on error the outputs are
  *    left as documented per call.  lasso_strerror() gives a message.
  *  - Pointers named *_host are host memory; pointers named d_* are device memory of the
@@ -114,16 +115,21 @@ typedef struct {
     int algo;                /* lasso_algo (default FISTA)                                      */
     int rule;                /* lasso_rule (default stable GAP Safe)                            */
     int screen_every;        /* screen every k passes (default 1)                               */
-    int max_iter;            /* per-signal pass limit (default 100000)                          */
+    int max_iter;            /* per-signal pass limit (default 20000)                           */
     int lambda_relative;     /* 1: lambdas are lambda / lambda_max of each signal (default 0)   */
     int final_fp64;          /* 1: append an FP64-accumulation rung on the exact data and keep
                                 FP64 iterates (tight tolerances; default 0)                     */
-    int certify_full;        /* 1: final full-dictionary pass for the reported gap (default 1)  */
+    int certify_full;        /* 1: audit with an explicit full-dictionary pass at exit (default
+                                0): every atom recomputed with error-free products            */
     int passes_per_sync;     /* passes per captured CUDA graph replay (default 8)               */
     int tensor_cores;        /* 1: batched BF16/FP8 levels use the tcgen05 GEMMs (default 1)   */
     double tau;              /* rejection guard: reject iff test < 1 - tau (default 1e-9)       */
     double time_limit_s;     /* 0: none                                                          */
     int profile;             /* 1: time every kernel of the passes with CUDA events (stats)     */
+    int full_gap;            /* 1: stop on the duality gap of the whole dictionary (default; the
+                                rejected atoms' correlations are evaluated when the preserved-set
+                                gap meets tol); 0: stop on the preserved-set gap, which bounds
+                                P(x) - P* only                                                  */
 } lasso_opts;
 
 /* Fill *opts with the defaults above. */

@@ -27,6 +27,7 @@ class LassoOpts(C.Structure):
         ("tau", C.c_double),
         ("time_limit_s", C.c_double),
         ("profile", C.c_int),
+        ("full_gap", C.c_int),
     ]
 
 

@@ -14,7 +14,7 @@ namespace lasso {
 
 constexpr int MAX_LEVELS = 8;
 constexpr int VEC_BYTES = 16;        // every dense row is padded to a multiple of 16 elements
-constexpr int CORR_CHUNK = 32;       // atoms of the preserved list per correlation work item
+constexpr int CORR_CHUNK = 32;       // smallest work item (atoms of the preserved list); batches use 4x
 constexpr int RES_THREADS = 256;
 
 // Arithmetic kind of a level.
@@ -40,9 +40,11 @@ struct LevelDev {
   const double* eps;        // eps_j >= ||a~_j - a_j|| (dictionary error only)
   const double* kappa;      // kappa_j: bound of sum_i |a~_ij| |v_i| / ||v|| (||a~_j|| or Kronecker form)
   const float* atnorm;      // ||a~_j||
+  const float* epsr32;      // eps_j + gam_corr kappa_j rounded up to FP32 (bulk bound in FP32 code)
   // Rounding of the correlation: |g^_j - a~_j^T rho^| <= gam_corr kappa_j ||rho^|| + 3 u_g |g^_j|,
   // so the stable test and the dual scaling use eps_j + gam_corr kappa_j in place of eps_j.
   double gam_corr;
+  double gam_tight;         // exact FP32 level: bound of the Dot2 recomputation (certificate)
   // Rounding of the residual, e_r >= ||rho^ - (y - A~ z)||:
   //   RES_FOLD:  gam_res sum_j |z_j| kappa_j + 2 u ||rho^||
   //   RES_CHAIN: gamma_{nnz+4}(u64) sum_j |z_j| kappa_j + 2 u ||rho^||
@@ -61,6 +63,8 @@ struct DictDev {
   int N, K, n_levels;
   int64_t ldN;              // padded signal length (multiple of 16)
   const double* anorm;      // exact ||a_j||_2, rounded up
+  const float* anorm32;     // the same rounded up to FP32
+  double amax;              // max_j ||a_j||_2
   LevelDev lv[MAX_LEVELS];
 };
 
@@ -70,6 +74,9 @@ struct SigState {
   double l1, sum_epsz, sum_kapz;     // of the current point z_t (its nonzero list)
   double gap, Gp, Gt, gamma, Rp, delta, sp;
   double lam_max_lb, lam_max_ub;
+  // snapshot of the pass whose reduced certificate met tol, awaiting the full-dictionary check
+  double c_rr, c_yr, c_l1, c_epsz, c_kapz, c_m1;
+  int c_nnz, pending, next_check, pad1;
   int level, n_kept, parity, n_nz, status, done, iters, Kt, n_chunks, pad0;
   int level_passes[MAX_LEVELS];
 };
@@ -83,6 +90,8 @@ struct SolveParams {
   double tol, Gamma, tau, L;
   int algo, rule, screen_every, max_iter;
   int B;
+  int chunk;                // atoms per correlation work item (multiple of CORR_CHUNK)
+  int full_gap;             // 1: stop on the full-dictionary gap (checked explicitly)
 };
 
 // ------------------------------------------------------------------ error-free transforms
@@ -133,6 +142,11 @@ __device__ __forceinline__ DF df_shfl_xor(const DF& v, int m) {
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, m));
   return v;
 }
 __device__ __forceinline__ double warp_max(double v) {

@@ -6,6 +6,8 @@
 // (eq:approx_dict, Section III-B); ladder {A~^i} with A~^I = A (Section IV); SuKro sums of
 // Kronecker products (Section V-A).
 #include <algorithm>
+#include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -257,6 +259,13 @@ __global__ void k_kron_dense_f32(const float* __restrict__ Bf, const float* __re
   }
 }
 
+// eps_j + gam kappa_j and ||a_j||, rounded up to FP32 (bounds used by FP32 device code).
+__global__ void k_round_up_f32(const double* __restrict__ eps, const double* __restrict__ kappa, double gam,
+                               int64_t K, float* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = __double2float_ru(kappa ? eps[j] + gam * kappa[j] : eps[j]);
+}
+
 // ------------------------------------------------------------------ power iteration kernels (FP64)
 
 __device__ __forceinline__ double level_elem(const LevelDev& L, int64_t j, int64_t n) {
@@ -395,27 +404,30 @@ static double host_mean_max(const double* dptr, int64_t K, double* mx) {
 static void level_rounding(const lasso_dict* d, const HostLevel& h, bool vt_double, LevelDev& L) {
   const double N = (double)d->ldN;
   const double stage = vt_double ? U32 : 0.0;   // rho rounded to FP32 for float arithmetic
-  const double nl = std::ceil(N / 32.0) + 6.0;   // per-lane chain + cross-lane levels
+  const double nl = std::ceil(N / 32.0) + 8.0;   // per-lane chain + cross-lane levels
   switch (h.kind) {
     case LK_F64:
     case LK_F32D:
       L.gam_corr = gamma_n(nl, U64);
+      L.gam_tight = L.gam_corr;
       L.res_model = RES_CHAIN;
       L.gam_res = 0.0;
       break;
     case LK_F32:
-      // Dot2: the error of s + c is <= 2 gamma_{2n}^2 sum |a_i rho_i| for a chain of n terms
-      L.gam_corr = 2.0 * gamma_n(2.0 * nl, U32) * gamma_n(2.0 * nl, U32) + stage;
+      // bulk passes: plain FMA chains of nl terms; certificate: Dot2, whose error is
+      // <= 2 gamma_{2n}^2 sum |a_i rho_i| for a chain of n terms
+      L.gam_corr = gamma_n(nl + 2.0, U32) + stage;
+      L.gam_tight = 2.0 * gamma_n(2.0 * nl, U32) * gamma_n(2.0 * nl, U32) + stage;
       L.res_model = RES_DOT2;
       L.gam_res = vt_double ? U32 : 0.0;          // z rounded to FP32 in the products
       break;
     case LK_BF16:
-      L.gam_corr = gamma_n(3.0, U32) + stage;
+      L.gam_corr = gamma_n(nl + 2.0, U32) + stage;
       L.res_model = RES_FOLD;
       L.gam_res = gamma_n(6.0, U32);
       break;
     case LK_FP8:
-      L.gam_corr = gamma_n(4.0, U32) + stage;
+      L.gam_corr = gamma_n(nl + 3.0, U32) + stage;
       L.res_model = RES_FOLD;
       L.gam_res = gamma_n(7.0, U32);
       break;
@@ -448,7 +460,23 @@ static void free_level(HostLevel& h) {
   cudaFree(h.eps);
   cudaFree(h.kappa);
   cudaFree(h.atnorm);
+  cudaFree(h.epsr32[0]);
+  cudaFree(h.epsr32[1]);
   h = HostLevel();
+}
+
+// FP32 copies of the per-atom bounds for the iterate precision of a solve (computed once).
+static int ensure_level_f32(const lasso_dict* d, const HostLevel& hc, bool vt_double, const LevelDev& L) {
+  HostLevel& h = const_cast<HostLevel&>(hc);
+  float*& dst = h.epsr32[vt_double ? 1 : 0];
+  if (dst) return LASSO_OK;
+  if (getenv("LASSO_TRACE_STEPS")) fprintf(stderr, "[lasso trace] level bounds: kind %d\n", h.kind);
+  LASSO_CUDA_TRY(cudaMalloc(&dst, d->K * sizeof(float)));
+  k_round_up_f32<<<grid_for(d->K), 256>>>(h.eps, h.kappa, L.gam_corr, d->K, dst);
+  LASSO_CUDA_TRY(cudaGetLastError());
+  // one-time set-up on the legacy stream: finish it before any solve stream reads the bounds
+  LASSO_CUDA_TRY(cudaDeviceSynchronize());
+  return LASSO_OK;
 }
 
 LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double) {
@@ -463,6 +491,8 @@ LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double)
   L.atnorm = h.atnorm;
   L.rc = h.rc;
   level_rounding(d, h, vt_double, L);
+  if (h.eps && ensure_level_f32(d, h, vt_double, L) == LASSO_OK) L.epsr32 = h.epsr32[vt_double ? 1 : 0];
+  else if (h.eps) L.epsr32 = nullptr;   // build_dict_dev rejects a level without its FP32 bounds
   if (h.kind == LK_KRON) {
     L.B = d->Bf;
     L.C = d->Cf;
@@ -483,15 +513,35 @@ int ensure_rung64(lasso_dict* d) {
   h = d->exact;               // shares the FP32 data and vectors of the exact level
   h.owns_data = false;
   h.kind = LK_F32D;
+  h.epsr32[0] = h.epsr32[1] = nullptr;
   return LASSO_OK;
 }
 
+static bool dict_trace() { return getenv("LASSO_TRACE_STEPS") != nullptr; }
+
 int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order) {
+  if (dict_trace()) fprintf(stderr, "[lasso trace] build_dict_dev: enter\n");
   memset(out, 0, sizeof(*out));
   out->N = (int)d->N;
   out->K = (int)d->K;
   out->ldN = d->ldN;
   out->anorm = d->anorm;
+  if (!d->anorm32) {
+    LASSO_CUDA_TRY(cudaMalloc(&d->anorm32, d->K * sizeof(float)));
+    k_round_up_f32<<<grid_for(d->K), 256>>>(d->anorm, nullptr, 0.0, d->K, d->anorm32);
+    LASSO_CUDA_TRY(cudaGetLastError());
+    LASSO_CUDA_TRY(cudaDeviceSynchronize());
+  }
+  out->anorm32 = d->anorm32;
+  if (d->anorm_max <= 0.0) {
+    std::vector<double> h(d->K);
+    LASSO_CUDA_TRY(cudaMemcpy(h.data(), d->anorm, d->K * sizeof(double), cudaMemcpyDeviceToHost));
+    double m = 0.0;
+    for (double v : h) m = std::max(m, v);
+    d->anorm_max = m;
+  }
+  out->amax = d->anorm_max;
+  if (dict_trace()) fprintf(stderr, "[lasso trace] build_dict_dev: atom norms ready\n");
   std::vector<const HostLevel*> lv;
   for (auto& h : d->approx) lv.push_back(&h);
   lv.push_back(&d->exact);
@@ -503,7 +553,10 @@ int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<con
   if ((int)lv.size() > MAX_LEVELS) return LASSO_ERR_INVALID_ARG;
   out->n_levels = (int)lv.size();
   const bool vt_double = final_fp64 || d->exact_kind == LK_F64;
-  for (size_t i = 0; i < lv.size(); ++i) out->lv[i] = make_level_dev(d, *lv[i], vt_double);
+  for (size_t i = 0; i < lv.size(); ++i) {
+    out->lv[i] = make_level_dev(d, *lv[i], vt_double);
+    if (!out->lv[i].epsr32) return LASSO_ERR_CUDA;
+  }
   if (order) *order = lv;
   return LASSO_OK;
 }
@@ -842,5 +895,10 @@ extern "C" void lasso_dict_destroy(lasso_dict* d) {
   cudaFree(d->gramB);
   cudaFree(d->gramC);
   cudaFree(d->anorm);
+  cudaFree(d->anorm32);
+  if (d->rung64.kind >= 0) {
+    cudaFree(d->rung64.epsr32[0]);
+    cudaFree(d->rung64.epsr32[1]);
+  }
   delete d;
 }

@@ -18,6 +18,7 @@ struct HostLevel {
   double* eps = nullptr;
   double* kappa = nullptr;
   float* atnorm = nullptr;
+  float* epsr32[2] = {nullptr, nullptr};   // per iterate precision (FP32, FP64)
   float* dscale = nullptr;     // Kronecker d_j as FP32
   double u = U32, gam_corr = 0.0, gam_res = 0.0, rc = 1.0;
   bool rc_set = false;
@@ -39,6 +40,8 @@ struct lasso_dict {
   double* gramB = nullptr;             // R x R x K1
   double* gramC = nullptr;             // R x R x K2
   double* anorm = nullptr;             // K, exact atom norms (rounded up)
+  float* anorm32 = nullptr;            // the same rounded up to FP32
+  double anorm_max = 0.0;              // max_j ||a_j||
   std::vector<lasso::HostLevel> approx;
   lasso::HostLevel exact;
   lasso::HostLevel rung64;             // FP64-accumulation rung on FP32 exact data (lazy)

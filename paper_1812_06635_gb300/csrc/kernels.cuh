@@ -130,6 +130,205 @@ __device__ __forceinline__ double warp_atom_dot(const LevelDev& L, int64_t j, in
   return 0.0;
 }
 
+// Fast warp dot product for the bulk of a pass: plain FMA chains (two independent FP32 or FP64
+// accumulators per lane), rho read through L1 straight from global memory.  The rounding error
+// is bounded by gamma_{ld/32 + 8} sum_i |a_i rho_i| (the LevelDev's gam_corr), which the stable
+// test absorbs; the certificate of the exact FP32 level is tightened separately (Dot2).
+template <typename VT>
+__device__ __forceinline__ float4 rho4_f(const VT* __restrict__ rho, int q) {
+  if constexpr (sizeof(VT) == 4) {
+    return __ldg(reinterpret_cast<const float4*>(rho) + q);
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(rho) + 2 * q;
+    double2 a = __ldg(p), b = __ldg(p + 1);
+    return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+  }
+}
+
+template <typename VT>
+__device__ __forceinline__ double warp_atom_dot_fast(const LevelDev& L, int64_t j, int ldN, const VT* __restrict__ rho,
+                                                     int lane) {
+  switch (L.kind) {
+    case LK_F32: {
+      const float4* row = reinterpret_cast<const float4*>((const float*)L.data + j * L.ld);
+      float s0 = 0.f, s1 = 0.f;
+      const int nv = ldN >> 2;
+      int k = lane;
+      for (; k + 32 < nv; k += 64) {
+        const float4 a = __ldg(row + k), b = __ldg(row + k + 32);
+        const float4 r = rho4_f(rho, k), t = rho4_f(rho, k + 32);
+        s0 = __fmaf_rn(a.x, r.x, s0); s0 = __fmaf_rn(a.y, r.y, s0); s0 = __fmaf_rn(a.z, r.z, s0); s0 = __fmaf_rn(a.w, r.w, s0);
+        s1 = __fmaf_rn(b.x, t.x, s1); s1 = __fmaf_rn(b.y, t.y, s1); s1 = __fmaf_rn(b.z, t.z, s1); s1 = __fmaf_rn(b.w, t.w, s1);
+      }
+      if (k < nv) {
+        const float4 a = __ldg(row + k);
+        const float4 r = rho4_f(rho, k);
+        s0 = __fmaf_rn(a.x, r.x, s0); s0 = __fmaf_rn(a.y, r.y, s0); s0 = __fmaf_rn(a.z, r.z, s0); s0 = __fmaf_rn(a.w, r.w, s0);
+      }
+      return warp_sum_f(__fadd_rn(s0, s1));
+    }
+    case LK_BF16: {
+      const uint4* row = reinterpret_cast<const uint4*>((const __nv_bfloat16*)L.data + j * L.ld);
+      float s0 = 0.f, s1 = 0.f;
+      const int nv = ldN >> 3;
+#pragma unroll 2
+      for (int k = lane; k < nv; k += 32) {
+        const uint4 a = __ldg(row + k);
+        const float4 r0 = rho4_f(rho, 2 * k), r1 = rho4_f(rho, 2 * k + 1);
+        const float2 a0 = bf16x2_to_f2(a.x), a1 = bf16x2_to_f2(a.y), a2 = bf16x2_to_f2(a.z), a3 = bf16x2_to_f2(a.w);
+        s0 = __fmaf_rn(a0.x, r0.x, s0); s1 = __fmaf_rn(a0.y, r0.y, s1);
+        s0 = __fmaf_rn(a1.x, r0.z, s0); s1 = __fmaf_rn(a1.y, r0.w, s1);
+        s0 = __fmaf_rn(a2.x, r1.x, s0); s1 = __fmaf_rn(a2.y, r1.y, s1);
+        s0 = __fmaf_rn(a3.x, r1.z, s0); s1 = __fmaf_rn(a3.y, r1.w, s1);
+      }
+      return warp_sum_f(__fadd_rn(s0, s1));
+    }
+    case LK_FP8: {
+      const uint4* row = reinterpret_cast<const uint4*>((const uint8_t*)L.data + j * L.ld);
+      float s0 = 0.f, s1 = 0.f;
+      const int nv = ldN >> 4;
+      for (int k = lane; k < nv; k += 32) {
+        const uint4 a = __ldg(row + k);
+        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 r = rho4_f(rho, 4 * k + q);
+          const float2 lo = fp8x2_to_f2((uint16_t)(w[q] & 0xffffu));
+          const float2 hi = fp8x2_to_f2((uint16_t)(w[q] >> 16));
+          s0 = __fmaf_rn(lo.x, r.x, s0); s1 = __fmaf_rn(lo.y, r.y, s1);
+          s0 = __fmaf_rn(hi.x, r.z, s0); s1 = __fmaf_rn(hi.y, r.w, s1);
+        }
+      }
+      return __fmul_rn(warp_sum_f(__fadd_rn(s0, s1)), L.scale[j]);
+    }
+    case LK_F64: {
+      const double2* row = reinterpret_cast<const double2*>((const double*)L.data + j * L.ld);
+      const double2* rs = reinterpret_cast<const double2*>(rho);
+      double s = 0.0;
+      const int nv = ldN >> 1;
+      for (int k = lane; k < nv; k += 32) {
+        const double2 a = __ldg(row + k);
+        const double2 r = __ldg(rs + k);
+        s = fma(a.x, r.x, s);
+        s = fma(a.y, r.y, s);
+      }
+      return warp_sum(s);
+    }
+    case LK_F32D: {
+      const float4* row = reinterpret_cast<const float4*>((const float*)L.data + j * L.ld);
+      const double2* rs = reinterpret_cast<const double2*>(rho);
+      double s = 0.0;
+      const int nv = ldN >> 2;
+      for (int k = lane; k < nv; k += 32) {
+        const float4 a = __ldg(row + k);
+        const double2 r0 = __ldg(rs + 2 * k), r1 = __ldg(rs + 2 * k + 1);
+        s = fma((double)a.x, r0.x, s);
+        s = fma((double)a.y, r0.y, s);
+        s = fma((double)a.z, r1.x, s);
+        s = fma((double)a.w, r1.y, s);
+      }
+      return warp_sum(s);
+    }
+  }
+  return 0.0;
+}
+
+// Two atoms at once with four 16-byte loads of each row in flight per lane (float levels only):
+// the correlation pass is bound by the bytes in flight from L2, not by arithmetic.  Same
+// rounding model as warp_atom_dot_fast (FP32 FMA chains, two accumulators per atom).
+template <typename VT>
+__device__ __forceinline__ void warp_atom_dot2_fast(const LevelDev& L, int64_t j0, int64_t j1, int ldN,
+                                                    const VT* __restrict__ rho, int lane, float& g0, float& g1) {
+  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+  if (L.kind == LK_F32) {
+    const float4* r0 = reinterpret_cast<const float4*>((const float*)L.data + j0 * L.ld);
+    const float4* r1 = reinterpret_cast<const float4*>((const float*)L.data + j1 * L.ld);
+    const int nv = ldN >> 2;
+    int k = lane;
+    for (; k + 32 < nv; k += 64) {
+      const float4 x0 = __ldg(r0 + k), x1 = __ldg(r0 + k + 32), y0 = __ldg(r1 + k), y1 = __ldg(r1 + k + 32);
+      const float4 p = rho4_f(rho, k), q = rho4_f(rho, k + 32);
+      a0 = __fmaf_rn(x0.x, p.x, a0); a0 = __fmaf_rn(x0.y, p.y, a0); a0 = __fmaf_rn(x0.z, p.z, a0); a0 = __fmaf_rn(x0.w, p.w, a0);
+      a1 = __fmaf_rn(x1.x, q.x, a1); a1 = __fmaf_rn(x1.y, q.y, a1); a1 = __fmaf_rn(x1.z, q.z, a1); a1 = __fmaf_rn(x1.w, q.w, a1);
+      b0 = __fmaf_rn(y0.x, p.x, b0); b0 = __fmaf_rn(y0.y, p.y, b0); b0 = __fmaf_rn(y0.z, p.z, b0); b0 = __fmaf_rn(y0.w, p.w, b0);
+      b1 = __fmaf_rn(y1.x, q.x, b1); b1 = __fmaf_rn(y1.y, q.y, b1); b1 = __fmaf_rn(y1.z, q.z, b1); b1 = __fmaf_rn(y1.w, q.w, b1);
+    }
+    if (k < nv) {
+      const float4 x0 = __ldg(r0 + k), y0 = __ldg(r1 + k);
+      const float4 p = rho4_f(rho, k);
+      a0 = __fmaf_rn(x0.x, p.x, a0); a0 = __fmaf_rn(x0.y, p.y, a0); a0 = __fmaf_rn(x0.z, p.z, a0); a0 = __fmaf_rn(x0.w, p.w, a0);
+      b0 = __fmaf_rn(y0.x, p.x, b0); b0 = __fmaf_rn(y0.y, p.y, b0); b0 = __fmaf_rn(y0.z, p.z, b0); b0 = __fmaf_rn(y0.w, p.w, b0);
+    }
+  } else if (L.kind == LK_BF16) {
+    const uint4* r0 = reinterpret_cast<const uint4*>((const __nv_bfloat16*)L.data + j0 * L.ld);
+    const uint4* r1 = reinterpret_cast<const uint4*>((const __nv_bfloat16*)L.data + j1 * L.ld);
+    const int nv = ldN >> 3;
+    int k = lane;
+    auto acc = [&](float& s0, float& s1, const uint4 a, const float4 p, const float4 q) {
+      const float2 e0 = bf16x2_to_f2(a.x), e1 = bf16x2_to_f2(a.y), e2 = bf16x2_to_f2(a.z), e3 = bf16x2_to_f2(a.w);
+      s0 = __fmaf_rn(e0.x, p.x, s0); s1 = __fmaf_rn(e0.y, p.y, s1);
+      s0 = __fmaf_rn(e1.x, p.z, s0); s1 = __fmaf_rn(e1.y, p.w, s1);
+      s0 = __fmaf_rn(e2.x, q.x, s0); s1 = __fmaf_rn(e2.y, q.y, s1);
+      s0 = __fmaf_rn(e3.x, q.z, s0); s1 = __fmaf_rn(e3.y, q.w, s1);
+    };
+    for (; k + 32 < nv; k += 64) {
+      const uint4 x0 = __ldg(r0 + k), x1 = __ldg(r0 + k + 32), y0 = __ldg(r1 + k), y1 = __ldg(r1 + k + 32);
+      const float4 p0 = rho4_f(rho, 2 * k), q0 = rho4_f(rho, 2 * k + 1);
+      const float4 p1 = rho4_f(rho, 2 * (k + 32)), q1 = rho4_f(rho, 2 * (k + 32) + 1);
+      acc(a0, a1, x0, p0, q0);
+      acc(a0, a1, x1, p1, q1);
+      acc(b0, b1, y0, p0, q0);
+      acc(b0, b1, y1, p1, q1);
+    }
+    if (k < nv) {
+      const uint4 x0 = __ldg(r0 + k), y0 = __ldg(r1 + k);
+      const float4 p0 = rho4_f(rho, 2 * k), q0 = rho4_f(rho, 2 * k + 1);
+      acc(a0, a1, x0, p0, q0);
+      acc(b0, b1, y0, p0, q0);
+    }
+  } else {   // LK_FP8
+    const uint4* r0 = reinterpret_cast<const uint4*>((const uint8_t*)L.data + j0 * L.ld);
+    const uint4* r1 = reinterpret_cast<const uint4*>((const uint8_t*)L.data + j1 * L.ld);
+    const int nv = ldN >> 4;
+    auto acc = [&](float& s0, float& s1, const uint4 a, int k) {
+      const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 r = rho4_f(rho, 4 * k + q);
+        const float2 lo = fp8x2_to_f2((uint16_t)(w[q] & 0xffffu));
+        const float2 hi = fp8x2_to_f2((uint16_t)(w[q] >> 16));
+        s0 = __fmaf_rn(lo.x, r.x, s0); s1 = __fmaf_rn(lo.y, r.y, s1);
+        s0 = __fmaf_rn(hi.x, r.z, s0); s1 = __fmaf_rn(hi.y, r.w, s1);
+      }
+    };
+    int k = lane;
+    for (; k + 32 < nv; k += 64) {
+      const uint4 x0 = __ldg(r0 + k), x1 = __ldg(r0 + k + 32), y0 = __ldg(r1 + k), y1 = __ldg(r1 + k + 32);
+      acc(a0, a1, x0, k);
+      acc(a0, a1, x1, k + 32);
+      acc(b0, b1, y0, k);
+      acc(b0, b1, y1, k + 32);
+    }
+    if (k < nv) {
+      const uint4 x0 = __ldg(r0 + k), y0 = __ldg(r1 + k);
+      acc(a0, a1, x0, k);
+      acc(b0, b1, y0, k);
+    }
+  }
+  float u = __fadd_rn(a0, a1), v = __fadd_rn(b0, b1);
+#pragma unroll
+  for (int m = 16; m; m >>= 1) {
+    u = __fadd_rn(u, __shfl_xor_sync(0xffffffffu, u, m));
+    v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, m));
+  }
+  if (L.kind == LK_FP8) {
+    u = __fmul_rn(u, L.scale[j0]);
+    v = __fmul_rn(v, L.scale[j1]);
+  }
+  g0 = u;
+  g1 = v;
+}
+
 // Four consecutive rows [r0, r0 + 4) of atom j (r0 a multiple of 4), as FP32 / FP64.
 __device__ __forceinline__ float4 load4_f(const LevelDev& L, int64_t j, int r0) {
   switch (L.kind) {

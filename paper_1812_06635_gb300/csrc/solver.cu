@@ -8,6 +8,7 @@
 // eq:DefRatioSwitch; look-ahead estimate eq:DefCardinalEstimated; ISTA update
 // eq:ISTA_update (FISTA momentum of Beck & Teboulle); stopping rule of Section IV.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cstring>
 #include <vector>
@@ -36,6 +37,11 @@ struct Workspace {
   void* nz_val = nullptr;
   int32_t* nz_idx = nullptr;
   int32_t* kept = nullptr;           // 2 x B x K
+  uint8_t* mask = nullptr;           // B x K, 1 while the atom is preserved
+  int32_t* cand_idx = nullptr;       // B x K, nonzeros of the point awaiting the full check
+  void* cand_val = nullptr;          // B x K
+  int32_t* offsets2 = nullptr;       // B + 1, work items of the full-dictionary checks
+  double* part_full = nullptr;       // B x nch
   float* c0ub = nullptr;             // B x K, |a_j^T y| upper bounds (Dynamic Safe rule)
   double* part_res = nullptr;        // B x nrb x 2
   double* part_corr = nullptr;       // B x nch x 2
@@ -56,6 +62,7 @@ struct Workspace {
 void free_ws(Workspace* w) {
   if (!w) return;
   void* ptrs[] = {w->Yw, w->Rho, w->X, w->Z, w->G, w->Xout, w->nz_val, w->nz_idx, w->kept, w->c0ub,
+                  w->mask, w->cand_idx, w->cand_val, w->offsets2, w->part_full,
                   w->part_res, w->part_corr, w->offsets, w->counters, w->alg_bytes, w->st, w->Gfull, w->AZ, w->Xd, w->Tk};
   for (void* p : ptrs) cudaFree(p);
   cudaFreeHost(w->h_counters);
@@ -105,6 +112,11 @@ static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
   rc |= ws_alloc(&w->nz_val, BK * vs);
   rc |= ws_alloc((void**)&w->nz_idx, BK * 4);
   rc |= ws_alloc((void**)&w->kept, 2 * BK * 4);
+  rc |= ws_alloc((void**)&w->mask, BK);
+  rc |= ws_alloc((void**)&w->cand_idx, BK * 4);
+  rc |= ws_alloc(&w->cand_val, BK * vs);
+  rc |= ws_alloc((void**)&w->offsets2, (size_t)(B + 1) * 4);
+  rc |= ws_alloc((void**)&w->part_full, (size_t)B * w->nch * 8);
   rc |= ws_alloc((void**)&w->c0ub, BK * 4);
   rc |= ws_alloc((void**)&w->part_res, (size_t)B * w->nrb * 2 * 8);
   rc |= ws_alloc((void**)&w->part_corr, (size_t)B * w->nch * 2 * 8);
@@ -144,6 +156,11 @@ struct PassArgs {
   VT* nz_val;
   int32_t* nz_idx;
   int32_t* kept;
+  uint8_t* mask;
+  int32_t* cand_idx;
+  VT* cand_val;
+  int32_t* offsets2;
+  double* part_full;
   float* c0ub;
   double* part_res;
   double* part_corr;
@@ -175,6 +192,40 @@ __device__ __forceinline__ int32_t* kept_of(const PassArgs<VT>& a, int b, int pa
   return a.kept + ((int64_t)parity * a.sp.B + b) * a.K;
 }
 
+// Every workspace pointer of a pass (one place, so no entry point can leave one unset).
+template <typename VT>
+static void fill_pass_args(PassArgs<VT>& pa, Workspace* w, const lasso_dict* d) {
+  pa.Yw = (const VT*)w->Yw;
+  pa.Rho = (VT*)w->Rho;
+  pa.X = (VT*)w->X;
+  pa.Z = (VT*)w->Z;
+  pa.G = (VT*)w->G;
+  pa.Xout = (VT*)w->Xout;
+  pa.nz_val = (VT*)w->nz_val;
+  pa.nz_idx = w->nz_idx;
+  pa.kept = w->kept;
+  pa.mask = w->mask;
+  pa.cand_idx = w->cand_idx;
+  pa.cand_val = (VT*)w->cand_val;
+  pa.offsets2 = w->offsets2;
+  pa.part_full = w->part_full;
+  pa.c0ub = w->c0ub;
+  pa.part_res = w->part_res;
+  pa.part_corr = w->part_corr;
+  pa.offsets = w->offsets;
+  pa.counters = w->counters;
+  pa.alg_bytes = w->alg_bytes;
+  pa.st = w->st;
+  pa.Gfull = w->Gfull;
+  pa.AZ = w->AZ;
+  pa.Xd = w->Xd;
+  pa.Tk = w->Tk;
+  pa.K = d->K;
+  pa.ldN = d->ldN;
+  pa.nrb = w->nrb;
+  pa.nch = w->nch;
+}
+
 // ------------------------------------------------------------------ init
 
 // ||y||^2, ||y||, FISTA scalars; the preserved set starts as every atom.
@@ -189,20 +240,24 @@ __global__ void k_init_state(PassArgs<VT> a, const double* __restrict__ lambdas)
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
   int32_t* kp = kept_of(a, b, 0);
-  for (int64_t j = threadIdx.x; j < a.K; j += blockDim.x) kp[j] = (int32_t)j;
+  uint8_t* mk = a.mask + (int64_t)b * a.K;
+  for (int64_t j = threadIdx.x; j < a.K; j += blockDim.x) {
+    kp[j] = (int32_t)j;
+    mk[j] = 1;
+  }
   if (threadIdx.x == 0) {
     double yy = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) yy += sh[w];
     SigState st;
     memset(&st, 0, sizeof(st));
-    st.lam = lambdas[b];
+    st.lam = lambdas ? lambdas[b] : 1.0;   // null: relative lambda 1 (lambda_max only)
     st.yy = yy;
     st.ynorm = sqrt(yy);
     st.t = 1.0;
     st.beta = 0.0;
     st.level = 0;
     st.n_kept = (int)a.K;
-    st.n_chunks = (int)((a.K + CORR_CHUNK - 1) / CORR_CHUNK);
+    st.n_chunks = (int)((a.K + a.sp.chunk - 1) / a.sp.chunk);
     st.gap = INFINITY;
     st.status = LASSO_OK;
     if (!(yy < INFINITY) || !(st.lam == st.lam)) {
@@ -424,13 +479,12 @@ enum CorrMode { CORR_PASS = 0, CORR_INIT = 1, CORR_CERT = 2 };
 // CORR_CERT: every atom with the most precise level, no update (full-dictionary certificate).
 template <typename VT, int MODE>
 __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_m1[CORR_THREADS / 32], s_m2[CORR_THREADS / 32];
-  __shared__ double s_nrho;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int B = a.sp.B;
   const int total = a.offsets[B];
   const int ldN = (int)a.ldN;
+  const int CH = a.sp.chunk;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     // signal of this item: last b with offsets[b] <= item
     int lo = 0, hi = B - 1;
@@ -446,64 +500,109 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
     const LevelDev& L = a.dd.lv[lvl];
     const bool fp64a = level_fp64_arith(L.kind);
     const int npos = MODE == CORR_PASS ? s.n_kept : (int)a.K;
-    const int p0 = chunk * CORR_CHUNK, p1 = min(npos, p0 + CORR_CHUNK);
+    const int p0 = chunk * CH, p1 = min(npos, p0 + CH);
     const VT* src = (MODE == CORR_INIT ? a.Yw : a.Rho) + (int64_t)b * a.ldN;
-    __syncthreads();
-    // stage rho (or y) in shared memory
-    if (L.kind != LK_KRON) {
-      if (fp64a) {
-        double* rd = reinterpret_cast<double*>(smem_raw);
-        for (int n = threadIdx.x; n < ldN; n += CORR_THREADS) rd[n] = (double)src[n];
-      } else {
-        float* rf = reinterpret_cast<float*>(smem_raw);
-        for (int n = threadIdx.x; n < ldN; n += CORR_THREADS) rf[n] = (float)src[n];
-      }
+    double rr = 0.0;
+    if (MODE == CORR_INIT) {
+      rr = s.yy;
+    } else {
+      for (int q = 0; q < a.nrb; ++q) rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
     }
-    if (threadIdx.x == 0) {
-      double rr = 0.0;
-      if (MODE == CORR_INIT) {
-        rr = s.yy;
-      } else {
-        for (int q = 0; q < a.nrb; ++q) rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
-      }
-      s_nrho = sqrt(rr);
-    }
-    __syncthreads();
-    const double nrho = s_nrho;
+    const double nrho = sqrt(rr);
     const double ug = fp64a && sizeof(VT) == 8 ? U64 : U32;
+    // the bulk pass bounds its rounding with gam_corr; INIT / CERT use the tight products
+    const double gam = MODE == CORR_PASS ? L.gam_corr : L.gam_tight;
     const double inv_L = 1.0 / a.sp.L;
     const double thr = s.lam * inv_L;
     const int32_t* kp = kept_of(a, b, s.parity);
     VT* X = a.X + (int64_t)b * a.K;
     VT* Z = a.Z + (int64_t)b * a.K;
     VT* G = a.G + (int64_t)b * a.K;
+    // per-atom epilogue: FP32 arithmetic for FP32 iterates (directed rounding keeps m1 an upper
+    // bound); FP64 only when the iterates are FP64
+    const float nrho_f = __double2float_ru(nrho);
+    const float ga_fac = 1.0000004f;   // >= 1 + 3 u32, rounded up
+    const float inv_Lf = (float)inv_L, thr_f = (float)thr, beta_f = (float)s.beta;
     double m1 = 0.0, m2 = 0.0;
-    for (int pos = p0 + wid; pos < p1; pos += CORR_THREADS / 32) {
-      const int64_t j = MODE == CORR_PASS ? kp[pos] : pos;
-      double g;
-      if (L.kind == LK_KRON) {
-        g = (double)a.Gfull[(int64_t)b * a.K + j];
+    float m1f = 0.f, m2f = 0.f;
+    const bool pair = MODE == CORR_PASS && (L.kind == LK_F32 || L.kind == LK_BF16 || L.kind == LK_FP8);
+    constexpr int NW = CORR_THREADS / 32;
+    for (int base = p0 + wid; base < p1; base += (pair ? 2 : 1) * NW) {
+      double gg[2] = {0.0, 0.0};
+      int64_t jj[2] = {0, 0};
+      int npair = 1;
+      jj[0] = MODE == CORR_PASS ? kp[base] : base;
+      if (pair && base + NW < p1) {
+        npair = 2;
+        jj[1] = kp[base + NW];
+        float f0, f1;
+        warp_atom_dot2_fast<VT>(L, jj[0], jj[1], ldN, src, lane, f0, f1);
+        gg[0] = f0;
+        gg[1] = f1;
+      } else if (L.kind == LK_KRON) {
+        gg[0] = (double)a.Gfull[(int64_t)b * a.K + jj[0]];
+      } else if (MODE == CORR_PASS) {
+        gg[0] = warp_atom_dot_fast<VT>(L, jj[0], ldN, src, lane);
       } else {
-        g = warp_atom_dot(L, j, ldN, reinterpret_cast<const float*>(smem_raw),
-                          reinterpret_cast<const double*>(smem_raw), lane);
+        gg[0] = warp_atom_dot(L, jj[0], ldN, reinterpret_cast<const float*>(src), reinterpret_cast<const double*>(src),
+                              lane);
       }
-      if (lane == 0) {
-        const double ga = fabs(g) * (1.0 + 3.0 * ug);
-        const double epsr = L.eps[j] + L.gam_corr * L.kappa[j];
-        m1 = fmax(m1, ga + epsr * nrho);
-        m2 = fmax(m2, fabs(g));
-        if (MODE == CORR_INIT) {
-          if (a.c0ub) a.c0ub[(int64_t)b * a.K + j] = __double2float_ru(ga + epsr * nrho);
-        } else if (MODE == CORR_PASS) {
-          const double xj = (double)X[j];
-          const double zj = (double)Z[j];
-          const double v = zj + g * inv_L;
-          const double xn = v > thr ? v - thr : (v < -thr ? v + thr : 0.0);
-          const double zn = a.sp.algo == LASSO_FISTA ? xn + s.beta * (xn - xj) : xn;
-          X[j] = (VT)xn;
-          Z[j] = (VT)zn;
-          G[pos] = (VT)g;
+      if (lane != 0) continue;
+      for (int q = 0; q < npair; ++q) {
+        const int64_t j = jj[q];
+        const int pos = base + q * NW;
+        if constexpr (sizeof(VT) == 4) {
+          const float g = (float)gg[q];
+          const float ag = fabsf(g);
+          // eps_j + gam kappa_j (FP32, rounded up); the INIT / CERT passes use the tight bound
+          const float er = MODE == CORR_PASS ? L.epsr32[j]
+                                             : __double2float_ru(L.eps[j] + gam * L.kappa[j]);
+          const float ub = __fmaf_ru(er, nrho_f, __fmul_ru(ag, ga_fac));
+          if (MODE == CORR_PASS) {
+            m1f = fmaxf(m1f, ub);
+            m2f = fmaxf(m2f, ag);
+          } else {
+            // INIT / CERT keep the unrounded error-free value (lambda_max, audit)
+            m1 = fmax(m1, fabs(gg[q]) * (1.0 + 4.0 * U64) + (L.eps[j] + gam * L.kappa[j]) * nrho);
+            m2 = fmax(m2, fabs(gg[q]));
+          }
+          if (MODE == CORR_INIT) {
+            if (a.c0ub) a.c0ub[(int64_t)b * a.K + j] = ub;
+          } else if (MODE == CORR_PASS) {
+            const float xj = (float)X[j];
+            const float zj = (float)Z[j];
+            const float v = __fmaf_rn(g, inv_Lf, zj);
+            const float xn = v > thr_f ? v - thr_f : (v < -thr_f ? v + thr_f : 0.f);
+            const float zn = a.sp.algo == LASSO_FISTA ? __fmaf_rn(beta_f, xn - xj, xn) : xn;
+            X[j] = (VT)xn;
+            Z[j] = (VT)zn;
+            G[pos] = (VT)g;
+          }
+        } else {
+          const double g = gg[q];
+          const double ga = fabs(g) * (1.0 + 3.0 * ug);
+          const double epsr = L.eps[j] + gam * L.kappa[j];
+          m1 = fmax(m1, ga + epsr * nrho);
+          m2 = fmax(m2, fabs(g));
+          if (MODE == CORR_INIT) {
+            if (a.c0ub) a.c0ub[(int64_t)b * a.K + j] = __double2float_ru(ga + epsr * nrho);
+          } else if (MODE == CORR_PASS) {
+            const double xj = (double)X[j];
+            const double zj = (double)Z[j];
+            const double v = zj + g * inv_L;
+            const double xn = v > thr ? v - thr : (v < -thr ? v + thr : 0.0);
+            const double zn = a.sp.algo == LASSO_FISTA ? xn + s.beta * (xn - xj) : xn;
+            X[j] = (VT)xn;
+            Z[j] = (VT)zn;
+            G[pos] = (VT)g;
+          }
         }
+      }
+    }
+    if constexpr (sizeof(VT) == 4) {
+      if (MODE == CORR_PASS) {
+        m1 = m1f;
+        m2 = m2f;
       }
     }
     if (lane == 0) {
@@ -528,6 +627,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
                                        (chunk == 0 ? a.dd.N * vs : 0.0));
       }
     }
+    __syncthreads();
   }
 }
 
@@ -539,7 +639,7 @@ __global__ void k_init_finish(PassArgs<VT> a, int lambda_relative) {
   SigState& s = a.st[b];
   if (s.done) return;
   double ub = 0.0, lb = 0.0;
-  const int nch = (int)((a.K + CORR_CHUNK - 1) / CORR_CHUNK);
+  const int nch = (int)((a.K + a.sp.chunk - 1) / a.sp.chunk);
   for (int c = 0; c < nch; ++c) {
     ub = fmax(ub, a.part_corr[((int64_t)b * a.nch + c) * 2]);
     lb = fmax(lb, a.part_corr[((int64_t)b * a.nch + c) * 2 + 1]);
@@ -558,7 +658,7 @@ __global__ void k_init_finish(PassArgs<VT> a, int lambda_relative) {
     s.n_kept = 0;
     s.status = LASSO_OK;
   }
-  s.n_chunks = (int)((s.n_kept + CORR_CHUNK - 1) / CORR_CHUNK);
+  s.n_chunks = (int)((s.n_kept + a.sp.chunk - 1) / a.sp.chunk);
 }
 
 // ------------------------------------------------------------------ gap, screening, switch
@@ -581,20 +681,11 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
   __shared__ int s_warp[SCREEN_THREADS / 32];
   __shared__ int s_warp2[SCREEN_THREADS / 32];
   __shared__ double s_red[3][SCREEN_THREADS / 32];
+  __shared__ double s_wmax[SCREEN_THREADS / 32];
   const int I = a.dd.n_levels - 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    SigState s = *sp;
-    const LevelDev& L = a.dd.lv[s.level];
-    double rr = 0.0, yr = 0.0, m1 = 0.0, m2 = 0.0;
-    for (int q = 0; q < a.nrb; ++q) {
-      rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
-      yr += a.part_res[((int64_t)b * a.nrb + q) * 2 + 1];
-    }
-    for (int c = 0; c < s.n_chunks; ++c) {
-      m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
-      m2 = fmax(m2, a.part_corr[((int64_t)b * a.nch + c) * 2 + 1]);
-    }
+  // FP64 scalars of the pass for a given upper bound m1 of max_j (|a_j^T rho| + eps_j ||rho||)
+  auto evaluate = [&](SigState& s, const LevelDev& L, double rr, double yr, double m1, double m2) {
     const double lam = s.lam;
     const double nrho = sqrt(rr);
     const double e_r = residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8);
@@ -608,41 +699,128 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
     const double P = 0.5 * rr + lam * s.l1;
     const double Dp = lam * sp_ * yr - 0.5 * lam * lam * sp_ * sp_ * rr;
     const double Dt = lam * st_ * yr - 0.5 * lam * lam * st_ * st_ * rr;
-    const double Gp = P - Dp, Gt = P - Dt;
-    const double delta = nrho * e + 0.5 * e * e;
-    const double Rp = sqrt(fmax(2.0 * Gp + 2.0 * delta, 0.0)) / lam;
-    const double Rt = sqrt(fmax(2.0 * Gt, 0.0)) / lam;
-    const double gamma = Gp > 0.0 ? Gt / Gp : 0.0;
-    const double gcert = fmax(Gp + delta, 0.0) / s.yy;
+    s.Gp = P - Dp;
+    s.Gt = P - Dt;
+    s.delta = nrho * e + 0.5 * e * e;
+    s.Rp = sqrt(fmax(2.0 * s.Gp + 2.0 * s.delta, 0.0)) / lam;
+    s.gamma = s.Gp > 0.0 ? s.Gt / s.Gp : 0.0;
+    s.sp = sp_;
+    sc[3] = fabs(st_);
+    sc[4] = sqrt(fmax(2.0 * s.Gt, 0.0)) / lam;
+    return fmax(s.Gp + s.delta, 0.0) / s.yy;   // certificate of the reduced problem (relative)
+  };
+  if (threadIdx.x == 0) {
+    SigState s = *sp;
+    const LevelDev& L = a.dd.lv[s.level];
+    double rr = 0.0, yr = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int q = 0; q < a.nrb; ++q) {
+      rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
+      yr += a.part_res[((int64_t)b * a.nrb + q) * 2 + 1];
+    }
+    for (int c = 0; c < s.n_chunks; ++c) {
+      m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
+      m2 = fmax(m2, a.part_corr[((int64_t)b * a.nch + c) * 2 + 1]);
+    }
+    const double gcert = evaluate(s, L, rr, yr, m1, m2);
     s.iters += 1;
     s.level_passes[s.level] += 1;
     if (a.alg_bytes) atomicAdd(&a.alg_bytes[8 + s.level], (double)s.n_kept);
-    s.Gp = Gp;
-    s.Gt = Gt;
-    s.gamma = gamma;
-    s.Rp = Rp;
-    s.delta = delta;
-    s.sp = sp_;
+    // The exact FP32 level bounds its bulk correlations loosely; when the gap without those
+    // margins already meets tol, the atoms that can attain the maximum are recomputed with
+    // error-free products (below) to tighten the certificate.
+    int refine = 0;
+    if (L.kind == LK_F32 && s.level == I && gcert > a.sp.tol && rr > 0.0 && m2 > 0.0) {
+      SigState t = s;
+      const double mest = m2 * (1.0 + 3.0 * U32);
+      if (evaluate(t, L, rr, yr, mest, m2) <= a.sp.tol) refine = 1;
+    }
+    sc[8] = rr;
+    sc[9] = yr;
+    sc[10] = m1;
+    sc[11] = m2;
+    sc[12] = gcert;
+    sc[13] = m1;
+    si[1] = refine;
+    *sp = s;
+  }
+  __syncthreads();
+  if (si[1]) {
+    // candidates: atoms whose loose upper bound exceeds max_j |g^_j|; every other atom is below it
+    const SigState& s = *sp;
+    const LevelDev& L = a.dd.lv[s.level];
+    const double T = sc[11], nrho = sqrt(sc[8]);
+    const int32_t* kp = kept_of(a, b, s.parity);
+    const VT* G = a.G + (int64_t)b * a.K;
+    const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
+    double wm = 0.0;
+    for (int pos = wid; pos < s.n_kept; pos += SCREEN_THREADS / 32) {
+      const int64_t j = kp[pos];
+      const double ub = fabs((double)G[pos]) * (1.0 + 3.0 * U32) + L.gam_corr * L.kappa[j] * nrho;
+      if (ub > T) {
+        const double g = warp_atom_dot(L, j, (int)a.ldN, rho, nullptr, lane);
+        wm = fmax(wm, fabs(g) * (1.0 + 3.0 * U32) + L.gam_tight * L.kappa[j] * nrho);
+      }
+    }
+    if (lane == 0) s_wmax[wid] = wm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m1 = T;
+      for (int w = 0; w < SCREEN_THREADS / 32; ++w) m1 = fmax(m1, s_wmax[w]);
+      SigState s2 = *sp;
+      sc[13] = fmin(m1, sc[10]);
+      sc[12] = evaluate(s2, L, sc[8], sc[9], sc[13], sc[11]);
+      *sp = s2;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    SigState s = *sp;
+    const LevelDev& L = a.dd.lv[s.level];
+    const double rr = sc[8], yr = sc[9], gcert = sc[12];
+    const double lam = s.lam;
+    const double nrho = sqrt(rr);
     int action = 0;   // 0 continue, 1 stop (converged), 2 stop (error)
-    if (!(rr < INFINITY) || !(yr == yr) || !(m1 < INFINITY) || !(Gp == Gp) || !(delta < INFINITY)) {
+    si[2] = 0;        // 1: snapshot the point for the full-dictionary check
+    if (!(rr < INFINITY) || !(yr == yr) || !(sc[10] < INFINITY) || !(s.Gp == s.Gp) || !(s.delta < INFINITY)) {
       s.status = LASSO_ERR_NONFINITE;
       action = 2;
-    } else if (s.level == I && gcert <= a.sp.tol) {
+    } else if (s.level == I && gcert <= a.sp.tol && !a.sp.full_gap) {
       s.status = LASSO_OK;
       action = 1;
+    } else if (s.level == I && gcert <= a.sp.tol && !s.pending && s.iters >= s.next_check) {
+      // the reduced problem is solved to tol: keep iterating while this point's correlations
+      // with the rejected atoms are checked (full-dictionary gap, stopping rule of Section IV)
+      s.pending = 1;
+      s.c_rr = rr;
+      s.c_yr = yr;
+      s.c_l1 = s.l1;
+      s.c_epsz = s.sum_epsz;
+      s.c_kapz = s.sum_kapz;
+      s.c_nnz = s.n_nz;
+      s.c_m1 = sc[13];
+      si[2] = 1;
     } else if (s.iters >= a.sp.max_iter) {
       s.status = LASSO_ERR_MAXITER;
       action = 2;
     }
     if (s.level == I || action) s.gap = gcert;
+    if (action) {
+      // the returned point's scalars (used by the optional full-dictionary audit)
+      s.c_rr = rr;
+      s.c_yr = yr;
+      s.c_l1 = s.l1;
+      s.c_epsz = s.sum_epsz;
+      s.c_kapz = s.sum_kapz;
+      s.c_nnz = s.n_nz;
+      s.c_m1 = sc[13];
+    }
     // Dynamic Safe radius ||theta' - y/lam|| (Table I)
+    const double sp_ = s.sp;
     const double d2 = sp_ * sp_ * rr - 2.0 * sp_ * yr / lam + s.yy / (lam * lam);
     const bool screen = rr > 0.0 && (s.iters % a.sp.screen_every) == 0;
     sc[0] = fabs(sp_);
     sc[1] = fabs(sp_) * nrho;
-    sc[2] = a.sp.rule == LASSO_RULE_GAP ? Rp : sqrt(fmax(d2, 0.0));
-    sc[3] = fabs(st_);
-    sc[4] = Rt;
+    sc[2] = a.sp.rule == LASSO_RULE_GAP ? s.Rp : sqrt(fmax(d2, 0.0));
     sc[5] = 1.0 - a.sp.tau;
     sc[6] = 1.0 + 3.0 * (level_fp64_arith(L.kind) && sizeof(VT) == 8 ? U64 : U32);
     sc[7] = 1.0 / lam;
@@ -665,25 +843,50 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
     if (threadIdx.x == 0) sp->done = 1;
     return;
   }
+  if (si[2]) {
+    for (int q = threadIdx.x; q < s.n_nz; q += SCREEN_THREADS) {
+      a.cand_idx[(int64_t)b * a.K + q] = a.nz_idx[(int64_t)b * a.K + q];
+      a.cand_val[(int64_t)b * a.K + q] = a.nz_val[(int64_t)b * a.K + q];
+    }
+  }
   const LevelDev& L = a.dd.lv[s.level];
   const bool screen = si[1];
   const double abs_sp = sc[0], c_eps = sc[1], Rs = sc[2], abs_st = sc[3], Rt = sc[4], thr = sc[5], gfac = sc[6],
                inv_lam = sc[7];
   const bool gap_rule = a.sp.rule == LASSO_RULE_GAP;
   const double* anorm = a.dd.anorm;
+  const float* anorm32 = a.dd.anorm32;
   const float* c0 = a.c0ub + (int64_t)b * a.K;
-  auto keep_of = [&](int pos, int64_t j) -> bool {
+  // FP32 copies of the scalars, rounded so that the FP32 test value stays an upper bound of
+  // the exact one (rejection needs test < 1 - tau, so over-estimating only keeps more atoms)
+  const float abs_sp_f = __double2float_ru(abs_sp), gfac_f = __double2float_ru(gfac);
+  const float c_eps_f = __double2float_ru(c_eps), Rs_f = __double2float_ru(Rs);
+  const float inv_lam_f = __double2float_ru(inv_lam), thr_f = __double2float_rd(thr);
+  const float abs_st_f = (float)abs_st, Rt_f = (float)Rt;
+  auto keep_of = [&](int pos, int64_t j, double& mu_out) -> bool {
     if (!screen) return true;
-    double mu;
-    if (gap_rule) mu = abs_sp * fabs((double)G[pos]) * gfac + (L.eps[j] + L.gam_corr * L.kappa[j]) * c_eps + Rs * anorm[j];
-    else mu = (double)c0[j] * inv_lam + Rs * anorm[j];
-    return mu >= thr;
+    if constexpr (sizeof(VT) == 4) {
+      float mu;
+      if (gap_rule)
+        mu = __fadd_ru(__fmaf_ru(L.epsr32[j], c_eps_f, __fmul_ru(__fmul_ru(abs_sp_f, fabsf((float)G[pos])), gfac_f)),
+                       __fmul_ru(Rs_f, anorm32[j]));
+      else
+        mu = __fadd_ru(__fmul_ru(c0[j], inv_lam_f), __fmul_ru(Rs_f, anorm32[j]));
+      mu_out = mu;
+      return mu >= thr_f;
+    } else {
+      double mu;
+      if (gap_rule) mu = abs_sp * fabs((double)G[pos]) * gfac + (L.eps[j] + L.gam_corr * L.kappa[j]) * c_eps + Rs * anorm[j];
+      else mu = (double)c0[j] * inv_lam + Rs * anorm[j];
+      mu_out = mu * (1.0 + 4.0 * U64);
+      return mu >= thr;
+    }
   };
   // ---- phase 1: look-ahead estimate K_t (conventional test on A~, eq:DefCardinalEstimated)
   int kt = 0;
   for (int pos = threadIdx.x; pos < s.n_kept; pos += SCREEN_THREADS) {
     const int64_t j = kp[pos];
-    if (abs_st * fabs((double)G[pos]) + Rt * (double)L.atnorm[j] >= 1.0) ++kt;
+    if (__fmaf_rn(abs_st_f, fabsf((float)G[pos]), Rt_f * L.atnorm[j]) >= 1.f) ++kt;
   }
   kt = warp_sum_i(kt);
   if (lane == 0) s_warp[wid] = kt;
@@ -716,10 +919,12 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
     double zv = 0.0;
     if (pos < s.n_kept) {
       j = kp[pos];
-      keep = keep_of(pos, j);
+      double mu = 0.0;
+      keep = keep_of(pos, j, mu);
       if (!keep) {
         X[j] = (VT)0;
         Z[j] = (VT)0;
+        a.mask[(int64_t)b * a.K + j] = 0;
       } else {
         zv = (double)Z[j];
         nz = zv != 0.0;
@@ -781,12 +986,141 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
     o.Kt = si[3];
     o.level = new_level;
     o.parity = s.parity ^ 1;
-    o.n_chunks = (base_k + CORR_CHUNK - 1) / CORR_CHUNK;
+    o.n_chunks = (base_k + a.sp.chunk - 1) / a.sp.chunk;
     // FISTA: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, momentum (t_k - 1) / t_{k+1} for the next update
     const double t1n = 0.5 * (1.0 + sqrt(1.0 + 4.0 * s.t * s.t));
     const double t2n = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t1n * t1n));
     o.t = t1n;
     o.beta = (t1n - 1.0) / t2n;
+  }
+}
+
+// ------------------------------------------------------------------ full-dictionary check
+
+// Work items of the pending checks: ceil(K / chunk) per pending signal.
+template <typename VT>
+__global__ void k_schedule_full(PassArgs<VT> a) {
+  __shared__ int sh_sum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int B = a.sp.B;
+  const int nchk = (int)((a.K + a.sp.chunk - 1) / a.sp.chunk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < B; base += blockDim.x) {
+    const int b = base + threadIdx.x;
+    const int items = (b < B && a.st[b].pending && !a.st[b].done) ? nchk : 0;
+    int v = items;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    if (lane == 31) sh_sum[wid] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int nw = blockDim.x >> 5;
+      int x = threadIdx.x < nw ? sh_sum[threadIdx.x] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)threadIdx.x >= o) x += t;
+      }
+      sh_sum[threadIdx.x] = x;
+    }
+    __syncthreads();
+    if (b < B) a.offsets2[b] = carry + (wid ? sh_sum[wid - 1] : 0) + v - items;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += sh_sum[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.offsets2[B] = carry;
+}
+
+// Correlations of the rejected atoms with the snapshot residual (fast products, rigorous
+// upper bounds with the exact level's margins); the preserved atoms are covered by c_m1.
+template <typename VT>
+__global__ void __launch_bounds__(CORR_THREADS) k_full_check(PassArgs<VT> a) {
+  __shared__ float s_m[CORR_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int B = a.sp.B;
+  const int total = a.offsets2[B];
+  const int CH = a.sp.chunk;
+  const LevelDev& L = a.dd.lv[a.dd.n_levels - 1];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (a.offsets2[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const int b = lo;
+    const int chunk = item - a.offsets2[b];
+    const SigState& s = a.st[b];
+    const VT* rho = a.Rho + (int64_t)b * a.ldN;
+    const uint8_t* mk = a.mask + (int64_t)b * a.K;
+    const float nrho_f = __double2float_ru(sqrt(s.c_rr));
+    const int64_t j0 = (int64_t)chunk * CH, j1 = min((int64_t)a.K, j0 + CH);
+    float m = 0.f;
+    for (int64_t j = j0 + wid; j < j1; j += CORR_THREADS / 32) {
+      if (mk[j]) continue;   // warp-uniform: every lane reads the same flag
+      const float g = (float)warp_atom_dot_fast<VT>(L, j, (int)a.ldN, rho, lane);
+      m = fmaxf(m, __fmaf_ru(L.epsr32[j], nrho_f, __fmul_ru(fabsf(g), 1.0000004f)));
+    }
+    if (lane == 0) s_m[wid] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < CORR_THREADS / 32; ++w) t = fmaxf(t, s_m[w]);
+      a.part_full[(int64_t)b * a.nch + chunk] = (double)t;
+    }
+    __syncthreads();
+  }
+}
+
+// Full-dictionary gap of the snapshot point; stop (and return it) when it meets tol.
+template <typename VT>
+__global__ void k_full_finish(PassArgs<VT> a) {
+  const int b = blockIdx.x;
+  SigState* sp = a.st + b;
+  __shared__ int s_stop, s_run;
+  // one thread reads the flags (thread 0 rewrites the state below), so the whole block agrees
+  if (threadIdx.x == 0) s_run = sp->pending && !sp->done;
+  __syncthreads();
+  if (!s_run) return;
+  if (threadIdx.x == 0) {
+    SigState s = *sp;
+    const LevelDev& L = a.dd.lv[a.dd.n_levels - 1];
+    const int nchk = (int)((a.K + a.sp.chunk - 1) / a.sp.chunk);
+    double m1 = s.c_m1;
+    for (int c = 0; c < nchk; ++c) m1 = fmax(m1, a.part_full[(int64_t)b * a.nch + c]);
+    const double lam = s.lam, rr = s.c_rr, yr = s.c_yr, nrho = sqrt(rr);
+    double sf = 0.0;
+    if (rr > 0.0) {
+      const double beta = yr / (lam * rr);
+      sf = m1 > 0.0 ? fmin(fmax(beta, -1.0 / m1), 1.0 / m1) : beta;
+    }
+    const double e = s.c_epsz + residual_bound(L, s.c_kapz, s.c_nnz, nrho, sizeof(VT) == 8);
+    const double P = 0.5 * rr + lam * s.c_l1;
+    const double D = lam * sf * yr - 0.5 * lam * lam * sf * sf * rr;
+    const double g = fmax(P - D + nrho * e + 0.5 * e * e, 0.0) / s.yy;
+    s.pending = 0;
+    s_stop = g <= a.sp.tol;
+    if (s_stop) {
+      s.gap = g;
+      s.status = LASSO_OK;
+    } else {
+      s.next_check = s.iters + 4;
+    }
+    *sp = s;
+  }
+  __syncthreads();
+  if (s_stop) {
+    VT* xo = a.Xout + (int64_t)b * a.K;
+    const int n = sp->c_nnz;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) xo[a.cand_idx[(int64_t)b * a.K + q]] = a.cand_val[(int64_t)b * a.K + q];
+    __syncthreads();
+    if (threadIdx.x == 0) sp->done = 1;
   }
 }
 
@@ -920,25 +1254,27 @@ __global__ void k_cert_finish(PassArgs<VT> a) {
   SigState& s = a.st[b];
   if (s.status != LASSO_OK || s.n_kept == 0 || s.iters == 0) return;
   const LevelDev& L = a.dd.lv[a.dd.n_levels - 1];
-  double rr = 0.0, yr = 0.0, m1 = 0.0;
-  for (int q = 0; q < a.nrb; ++q) {
-    rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
-    yr += a.part_res[((int64_t)b * a.nrb + q) * 2 + 1];
-  }
-  const int nch = (int)((a.K + CORR_CHUNK - 1) / CORR_CHUNK);
+  // the returned point's residual is the last one computed for this signal
+  const double rr = s.c_rr, yr = s.c_yr;
+  double m1 = 0.0;
+  const int nch = (int)((a.K + a.sp.chunk - 1) / a.sp.chunk);
   for (int c = 0; c < nch; ++c) m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
   const double lam = s.lam, nrho = sqrt(rr);
-  const double e = s.sum_epsz + residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8);
+  const double e = s.c_epsz + residual_bound(L, s.c_kapz, s.c_nnz, nrho, sizeof(VT) == 8);
   double sp_ = 0.0;
   if (rr > 0.0) {
     const double beta = yr / (lam * rr);
     sp_ = m1 > 0.0 ? fmin(fmax(beta, -1.0 / m1), 1.0 / m1) : beta;
   }
-  const double P = 0.5 * rr + lam * s.l1;
+  const double P = 0.5 * rr + lam * s.c_l1;
   const double D = lam * sp_ * yr - 0.5 * lam * lam * sp_ * sp_ * rr;
   const double g = fmax(P - D + nrho * e + 0.5 * e * e, 0.0) / s.yy;
-  s.gap = fmax(g, s.gap);
-  if (s.gap > a.sp.tol) s.status = LASSO_WARN_AUDIT;
+  // the audit recomputes every bound along another rounding path; unsafe screening would show
+  // as a gross excess, while a gap certified just below tol may come out a few ulps above it
+  if (g > a.sp.tol * (1.0 + 1e-3)) {
+    s.status = LASSO_WARN_AUDIT;
+    s.gap = fmax(g, s.gap);
+  }
 }
 
 template <typename VT>
@@ -970,6 +1306,26 @@ __global__ void k_load_y(PassArgs<VT> a, const float* __restrict__ Yf, const dou
 }
 
 // ------------------------------------------------------------------ host driver
+
+// Optional step tracing (environment LASSO_TRACE_STEPS=1): after a launch, poll the stream for at
+// most 10 s and report on stderr whether the step completed.  Diagnostics only.
+static bool trace_steps() {
+  static int v = -1;
+  if (v < 0) v = getenv("LASSO_TRACE_STEPS") != nullptr;
+  return v == 1;
+}
+
+static void trace_step(cudaStream_t st, const char* name) {
+  if (!trace_steps()) return;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaError_t q = cudaStreamQuery(st);
+  while (q == cudaErrorNotReady &&
+         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() < 10.0)
+    q = cudaStreamQuery(st);
+  fprintf(stderr, "[lasso trace] %-28s %s (%.3f s)\n", name,
+          q == cudaSuccess ? "done" : (q == cudaErrorNotReady ? "NOT DONE after 10 s" : cudaGetErrorString(q)),
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+}
 
 int g_num_sms = 0;
 
@@ -1045,12 +1401,17 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   k_corr<VT, CORR_PASS><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
   k_screen<VT><<<B, SCREEN_THREADS, 0, st>>>(pa);
+  if (pa.sp.full_gap) {
+    k_schedule_full<VT><<<1, 1024, 0, st>>>(pa);
+    k_full_check<VT><<<corr_grid, CORR_THREADS, 0, st>>>(pa);
+    k_full_finish<VT><<<B, 128, 0, st>>>(pa);
+  }
   if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
   k_schedule<VT><<<1, 1024, 0, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
 }
 
-static int pass_launches(bool has_kron) { return has_kron ? 9 : 4; }
+static int pass_launches(bool has_kron, bool full_gap) { return (has_kron ? 9 : 4) + (full_gap ? 3 : 0); }
 
 template <typename VT>
 static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats* stats) {
@@ -1080,30 +1441,9 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   pa.sp.screen_every = std::max(1, o.screen_every);
   pa.sp.max_iter = std::max(1, o.max_iter);
   pa.sp.B = (int)B;
-  pa.Yw = (const VT*)w->Yw;
-  pa.Rho = (VT*)w->Rho;
-  pa.X = (VT*)w->X;
-  pa.Z = (VT*)w->Z;
-  pa.G = (VT*)w->G;
-  pa.Xout = (VT*)w->Xout;
-  pa.nz_val = (VT*)w->nz_val;
-  pa.nz_idx = w->nz_idx;
-  pa.kept = w->kept;
-  pa.c0ub = w->c0ub;
-  pa.part_res = w->part_res;
-  pa.part_corr = w->part_corr;
-  pa.offsets = w->offsets;
-  pa.counters = w->counters;
-  pa.alg_bytes = w->alg_bytes;
-  pa.st = w->st;
-  pa.Gfull = w->Gfull;
-  pa.AZ = w->AZ;
-  pa.Xd = w->Xd;
-  pa.Tk = w->Tk;
-  pa.K = d->K;
-  pa.ldN = d->ldN;
-  pa.nrb = w->nrb;
-  pa.nch = w->nch;
+  pa.sp.chunk = B >= 64 ? 4 * CORR_CHUNK : CORR_CHUNK;
+  pa.sp.full_gap = o.full_gap ? 1 : 0;
+  fill_pass_args(pa, w, d);
   const size_t vs = sizeof(VT);
   const size_t BK = (size_t)B * d->K;
   LASSO_CUDA_TRY(cudaMemsetAsync(w->X, 0, BK * vs, st));
@@ -1114,7 +1454,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   k_load_y<VT><<<dim3((unsigned)((d->ldN + 255) / 256), (unsigned)B), 256, 0, st>>>(pa, io.Yf, io.Yd);
   k_init_state<VT><<<(unsigned)B, 256, 0, st>>>(pa, io.lambdas);
   // smem for the staged vector
-  size_t corr_smem = (size_t)d->ldN * 8;
+  size_t corr_smem = 0;
   static bool attr_set[2] = {false, false};
   if (!attr_set[vs == 8]) {
     cudaFuncSetAttribute(k_corr<VT, CORR_PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1202,11 +1542,11 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   double hbytes[16] = {0};
   LASSO_CUDA_TRY(cudaMemcpyAsync(hbytes, w->alg_bytes, sizeof(hbytes), cudaMemcpyDeviceToHost, st));
   LASSO_CUDA_TRY(cudaStreamSynchronize(st));
-  int64_t launches = 6 + replays * (int64_t)k * pass_launches(has_kron);
+  int64_t launches = 6 + replays * (int64_t)k * pass_launches(has_kron, pa.sp.full_gap != 0);
   if (o.certify_full && result == LASSO_OK) {
     // certificate over every atom (offsets: K / CHUNK items per signal)
     std::vector<int32_t> offs(B + 1);
-    const int nch = (int)((d->K + CORR_CHUNK - 1) / CORR_CHUNK);
+    const int nch = (int)((d->K + pa.sp.chunk - 1) / pa.sp.chunk);
     for (int64_t b = 0; b <= B; ++b) offs[b] = (int32_t)(b * nch);
     LASSO_CUDA_TRY(cudaMemcpyAsync(w->offsets, offs.data(), (B + 1) * 4, cudaMemcpyHostToDevice, st));
     k_corr<VT, CORR_CERT><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
@@ -1230,7 +1570,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     stats->lambda_max = hs[0].lam_max_lb;
     stats->lambda = hs[0].lam;
     stats->launches = launches;
-    const int per_pass[6] = {1, 1, 1, 1, has_kron ? 5 : 0, 0};
+    const int per_pass[6] = {1, 1, pa.sp.full_gap ? 4 : 1, 1, has_kron ? 5 : 0, 0};
     for (int q = 0; q < 6; ++q) {
       stats->kernel_launches[q] = replays * (int64_t)k * per_pass[q];
       stats->kernel_ms[q] = kms[q];
@@ -1255,15 +1595,16 @@ extern "C" void lasso_opts_default(lasso_opts* o) {
   o->algo = LASSO_FISTA;
   o->rule = LASSO_RULE_GAP;
   o->screen_every = 1;
-  o->max_iter = 100000;
+  o->max_iter = 20000;
   o->lambda_relative = 0;
   o->final_fp64 = 0;
-  o->certify_full = 1;
+  o->certify_full = 0;
   o->passes_per_sync = 8;
   o->tensor_cores = 1;
   o->tau = 1e-9;
   o->time_limit_s = 0.0;
   o->profile = 0;
+  o->full_gap = 1;
 }
 
 static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
@@ -1384,39 +1725,27 @@ static int run_lambda_max(lasso_dict* d, Workspace* w, const float* Y, int64_t B
   PassArgs<VT> pa;
   memset(&pa, 0, sizeof(pa));
   int rc = build_dict_dev(d, false, &pa.dd, nullptr);
+  if (trace_steps()) fprintf(stderr, "[lasso trace] lmax: levels built rc %d\n", rc);
   if (rc) return rc;
   pa.sp.B = (int)B;
   pa.sp.L = 1.0;
-  pa.Yw = (const VT*)w->Yw;
-  pa.Rho = (VT*)w->Rho;
-  pa.kept = w->kept;
-  pa.c0ub = w->c0ub;
-  pa.part_res = w->part_res;
-  pa.part_corr = w->part_corr;
-  pa.offsets = w->offsets;
-  pa.counters = w->counters;
-  pa.st = w->st;
-  pa.X = (VT*)w->X;
-  pa.Z = (VT*)w->Z;
-  pa.G = (VT*)w->G;
-  pa.K = d->K;
-  pa.ldN = d->ldN;
-  pa.nrb = w->nrb;
-  pa.nch = w->nch;
-  double* ones = nullptr;
-  LASSO_CUDA_TRY(cudaMalloc(&ones, B * 8));
-  std::vector<double> h(B, 1.0);
-  cudaMemcpyAsync(ones, h.data(), B * 8, cudaMemcpyHostToDevice, st);
+  pa.sp.chunk = CORR_CHUNK;
+  fill_pass_args(pa, w, d);
+  if (trace_steps()) fprintf(stderr, "[lasso trace] lmax: arguments ready\n");
   k_load_y<VT><<<dim3((unsigned)((d->ldN + 255) / 256), (unsigned)B), 256, 0, st>>>(pa, Y, nullptr);
-  k_init_state<VT><<<(unsigned)B, 256, 0, st>>>(pa, ones);
-  cudaFuncSetAttribute(k_corr<VT, CORR_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  trace_step(st, "lmax: k_load_y");
+  k_init_state<VT><<<(unsigned)B, 256, 0, st>>>(pa, nullptr);
+  trace_step(st, "lmax: k_init_state");
   k_schedule<VT><<<1, 1024, 0, st>>>(pa);
-  k_corr<VT, CORR_INIT><<<num_sms() * 8, CORR_THREADS, (size_t)d->ldN * 8, st>>>(pa);
+  trace_step(st, "lmax: k_schedule");
+  k_corr<VT, CORR_INIT><<<num_sms() * 8, CORR_THREADS, 0, st>>>(pa);
+  trace_step(st, "lmax: k_corr init");
   k_init_finish<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa, 1);
+  trace_step(st, "lmax: k_init_finish");
   k_copy_lmax<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa, out);
+  trace_step(st, "lmax: k_copy_lmax");
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(ones);
   if (e != cudaSuccess) {
     set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
     return LASSO_ERR_CUDA;
@@ -1428,10 +1757,13 @@ extern "C" int lasso_lambda_max(lasso_dict* d, const float* d_Y, int64_t B, doub
   if (!d || !d_Y || !d_out || B <= 0) return LASSO_ERR_INVALID_ARG;
   const bool vt_double = d->exact_kind == LK_F64;
   Workspace* w = nullptr;
+  if (trace_steps()) fprintf(stderr, "[lasso trace] lmax: enter (stream %p)\n", stream);
   int rc = get_ws(d, B, vt_double, &w);
+  if (trace_steps()) fprintf(stderr, "[lasso trace] lmax: workspace rc %d\n", rc);
   if (rc) return rc;
   cudaStream_t st = stream ? (cudaStream_t)stream : w->stream;
   if (!stream) LASSO_CUDA_TRY(cudaStreamSynchronize(0));
+  if (trace_steps()) fprintf(stderr, "[lasso trace] lmax: legacy stream synchronised\n");
   if (vt_double) return run_lambda_max<double>(d, w, d_Y, B, d_out, st);
   return run_lambda_max<float>(d, w, d_Y, B, d_out, st);
 }

@@ -1,0 +1,52 @@
+"""Write the oracle reference solutions used by the GPU tests (calls only oracle/ and synthetic/).
+
+    python tests/golden/make_references.py
+
+c3_reference.npz: for a few signals of the c3 batch (2048 x 8192, seed 0) the Lasso minimiser at
+lambda = ratio * lambda_max, computed by the FP64 oracle (FISTA + GAP Safe, then the KKT-verified
+support system), stored sparsely (support, values), with lambda_max and lambda.
+"""
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import synthetic as S                      # noqa: E402
+from oracle import lasso as OL             # noqa: E402
+from oracle import solvers as OS           # noqa: E402
+
+C3_SIGNALS = (0, 1, 2, 4095)
+
+
+def minimiser(A, y, lam):
+    for tol in (1e-9, 1e-11, 1e-13):
+        r = OS.fista_gap_safe(A, y, lam, tol, max_iter=400000)
+        x, ok = OS.kkt_polish(A, y, lam, r.x)
+        if ok:
+            return x
+    raise RuntimeError("oracle did not identify the support")
+
+
+def c3_reference(path):
+    w = S.c3(n_signals=4096)
+    out = {}
+    for b in C3_SIGNALS:
+        y = w.Y[b]
+        lm = OL.lambda_max(w.A.T @ y)
+        lam = float(w.lam_ratio[b]) * lm
+        x = minimiser(w.A, y, lam)
+        S_ = np.flatnonzero(x)
+        out[f"s{b}_idx"] = S_.astype(np.int32)
+        out[f"s{b}_val"] = x[S_]
+        out[f"s{b}_lmax"] = np.array(lm)
+        out[f"s{b}_lam"] = np.array(lam)
+        print(b, "support", S_.size, "lambda/lambda_max", w.lam_ratio[b])
+    out["signals"] = np.array(C3_SIGNALS)
+    np.savez_compressed(path, **out)
+
+
+if __name__ == "__main__":
+    c3_reference(os.path.join(HERE, "c3_reference.npz"))

@@ -37,7 +37,7 @@ def test_host_only_calls(lib):
     from paper_1812_06635_gb300 import _native
     o = _native.LassoOpts()
     lib.lasso_opts_default(C.byref(o))
-    assert o.Gamma == 0.5 and o.screen_every == 1 and o.certify_full == 1 and o.passes_per_sync == 8
+    assert o.Gamma == 0.5 and o.screen_every == 1 and o.certify_full == 0 and o.passes_per_sync == 8
     assert lib.lasso_strerror(-4).decode().startswith("iteration limit")
     assert b"sm_103a" in lib.lasso_build_info()
     # argument validation happens before any device call
