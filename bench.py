@@ -313,6 +313,15 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "avg_launch_us": 1e3 * kms[kind] / max(1.0, klaunch[kind]),
                 "kernel_share": {names[i]: kms[i] / max(1e-9, kms.sum()) for i in range(6) if kms[i] > 0}}
+    # the tensor-core stage (quantisation + tcgen05 correlation of the FP8 / BF16 levels)
+    roofline_tc = None
+    if kms[5] > 0:
+        tflops = kbytes[5] / (kms[5] * 1e-3) / 1e12
+        roofline_tc = {"bound": "tensor", "achieved": tflops, "peak": bf16, "unit": "TFLOP/s",
+                       "frac": tflops / bf16, "kernel": "k_tc_corr (+ k_quant_rho)",
+                       "peak_source": "measured bf16 (MEASURED_PEAKS.json bf16_tflops); FP8 passes counted "
+                                      "against the same BF16 peak",
+                       "algorithmic_flops_per_launch": kbytes[5] / max(1.0, klaunch[5] / 2)}
 
     line = None
     if rank == 0:
@@ -338,7 +347,8 @@ def run_ours(args):
                 "solved_per_step": solved / args.steps, "signals_per_step": B * world,
                 "e2e": {"value": e2e_solved / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(B * w.N * 4 + B * 8),
                         "d2h_bytes_per_step": int(B * w.K * 4 + B * 8 + B * 4)},
-                "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "comparator": comp,
+                "gpu_launches": int(launches), "roofline": roofline, "roofline_tensor": roofline_tc,
+                "cpu_baseline": cpu, "comparator": comp,
                 "clocks": clk, "passes_max": st.passes,
                 "level_passes_per_signal": [v / B for v in st.level_passes[:3]],
                 "level_atom_passes_per_signal": [v / B for v in st.level_atoms[:3]]}

@@ -201,6 +201,14 @@ int lasso_lambda_max_noalloc(const lasso_dict* dict, const float* d_Y, int64_t B
 int lasso_backward(lasso_dict* dict, const float* d_Y, const float* d_X, const float* d_G,
                    int64_t B, float* d_dY, float* d_dA, void* stream);
 
+/* Check of the tensor-core GEMM behind the batched BF16 / FP8 levels: B x K correlations of
+ * random operands (N terms each; signed values, and all-positive values for the worst
+ * accumulation) through tcgen05, compared with an FP64 evaluation of the same products.
+ * max_rel_err: largest |error| / sum_i |a_i r_i|; max_err_over_bound: largest |error| over the
+ * accumulation bound the stable test assumes (gamma_{N + N/k}(u_tc) sum_i |a_i r_i|, with
+ * u_tc = 2^-22 for BF16 and 2^-19 for E4M3).  fp8: 1 = E4M3, 0 = BF16. */
+int lasso_tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel_err, double* max_err_over_bound);
+
 const char* lasso_strerror(int status);
 
 /* Build information ("sm_103a ..."). */

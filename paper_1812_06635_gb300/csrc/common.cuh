@@ -41,6 +41,10 @@ struct LevelDev {
   const double* kappa;      // kappa_j: bound of sum_i |a~_ij| |v_i| / ||v|| (||a~_j|| or Kronecker form)
   const float* atnorm;      // ||a~_j||
   const float* epsr32;      // eps_j + gam_corr kappa_j rounded up to FP32 (bulk bound in FP32 code)
+  const float* kappa32;     // kappa_j rounded up to FP32
+  int tc;                   // 1: batched correlation on the tensor cores (BF16 / FP8 levels)
+  void* rq;                 // tensor-core levels: quantised residuals (B x ld, BF16 or E4M3)
+  float* rsig;              // tensor-core levels: per-signal scale of the quantised residual
   // Rounding of the correlation: |g^_j - a~_j^T rho^| <= gam_corr kappa_j ||rho^|| + 3 u_g |g^_j|,
   // so the stable test and the dual scaling use eps_j + gam_corr kappa_j in place of eps_j.
   double gam_corr;
@@ -76,6 +80,7 @@ struct SigState {
   double lam_max_lb, lam_max_ub;
   // snapshot of the pass whose reduced certificate met tol, awaiting the full-dictionary check
   double c_rr, c_yr, c_l1, c_epsz, c_kapz, c_m1;
+  double dq;                         // ||rho - rho^||: quantisation of the tensor-core operand
   int c_nnz, pending, next_check, pad1;
   int level, n_kept, parity, n_nz, status, done, iters, Kt, n_chunks, pad0;
   int level_passes[MAX_LEVELS];

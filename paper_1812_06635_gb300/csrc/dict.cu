@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "dict.cuh"
+#include "tc_gemm.cuh"
 
 namespace lasso {
 
@@ -401,10 +402,20 @@ static double host_mean_max(const double* dptr, int64_t K, double* mx) {
 // Rounding constants of a level for a solve iterating in FP32 (vt_double = false) or FP64.
 // Dense float levels: BF16 / FP8 fold 2 products into a double-float accumulator; the exact
 // FP32 level uses error-free products (TwoProduct + TwoSum), so its error is second order.
-static void level_rounding(const lasso_dict* d, const HostLevel& h, bool vt_double, LevelDev& L) {
+static void level_rounding(const lasso_dict* d, const HostLevel& h, bool vt_double, bool tc, LevelDev& L) {
   const double N = (double)d->ldN;
   const double stage = vt_double ? U32 : 0.0;   // rho rounded to FP32 for float arithmetic
   const double nl = std::ceil(N / 32.0) + 8.0;   // per-lane chain + cross-lane levels
+  if (tc && (h.kind == LK_BF16 || h.kind == LK_FP8)) {
+    // tensor-core accumulation of N products (k-steps of 16 BF16 / 32 E4M3), then the atom and
+    // signal scales and the FP32 store
+    const bool f8 = h.kind == LK_FP8;
+    L.gam_corr = gamma_n(N + N / (f8 ? 32.0 : 16.0) + 3.0, f8 ? TC_U_FP8 : TC_U_BF16) + stage;
+    L.gam_tight = L.gam_corr;
+    L.res_model = RES_FOLD;
+    L.gam_res = gamma_n(f8 ? 7.0 : 6.0, U32);
+    return;
+  }
   switch (h.kind) {
     case LK_F64:
     case LK_F32D:
@@ -460,15 +471,21 @@ static void free_level(HostLevel& h) {
   cudaFree(h.eps);
   cudaFree(h.kappa);
   cudaFree(h.atnorm);
-  cudaFree(h.epsr32[0]);
-  cudaFree(h.epsr32[1]);
+  for (auto* e : h.epsr32) cudaFree(e);
+  if (h.owns_data || h.kind == LK_KRON) cudaFree(h.kappa32);
   h = HostLevel();
 }
 
 // FP32 copies of the per-atom bounds for the iterate precision of a solve (computed once).
-static int ensure_level_f32(const lasso_dict* d, const HostLevel& hc, bool vt_double, const LevelDev& L) {
+static int ensure_level_f32(const lasso_dict* d, const HostLevel& hc, bool vt_double, bool tc, const LevelDev& L) {
   HostLevel& h = const_cast<HostLevel&>(hc);
-  float*& dst = h.epsr32[vt_double ? 1 : 0];
+  if (!h.kappa32) {
+    LASSO_CUDA_TRY(cudaMalloc(&h.kappa32, d->K * sizeof(float)));
+    k_round_up_f32<<<grid_for(d->K), 256>>>(h.kappa, nullptr, 0.0, d->K, h.kappa32);
+    LASSO_CUDA_TRY(cudaGetLastError());
+    LASSO_CUDA_TRY(cudaDeviceSynchronize());
+  }
+  float*& dst = h.epsr32[(vt_double ? 1 : 0) + (tc ? 2 : 0)];
   if (dst) return LASSO_OK;
   if (getenv("LASSO_TRACE_STEPS")) fprintf(stderr, "[lasso trace] level bounds: kind %d\n", h.kind);
   LASSO_CUDA_TRY(cudaMalloc(&dst, d->K * sizeof(float)));
@@ -479,7 +496,7 @@ static int ensure_level_f32(const lasso_dict* d, const HostLevel& hc, bool vt_do
   return LASSO_OK;
 }
 
-LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double) {
+LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double, bool tc) {
   LevelDev L;
   memset(&L, 0, sizeof(L));
   L.kind = h.kind;
@@ -490,9 +507,15 @@ LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double)
   L.kappa = h.kappa;
   L.atnorm = h.atnorm;
   L.rc = h.rc;
-  level_rounding(d, h, vt_double, L);
-  if (h.eps && ensure_level_f32(d, h, vt_double, L) == LASSO_OK) L.epsr32 = h.epsr32[vt_double ? 1 : 0];
-  else if (h.eps) L.epsr32 = nullptr;   // build_dict_dev rejects a level without its FP32 bounds
+  tc = tc && (h.kind == LK_BF16 || h.kind == LK_FP8);
+  L.tc = tc ? 1 : 0;
+  level_rounding(d, h, vt_double, tc, L);
+  if (h.eps && ensure_level_f32(d, h, vt_double, tc, L) == LASSO_OK) {
+    L.epsr32 = h.epsr32[(vt_double ? 1 : 0) + (tc ? 2 : 0)];
+    L.kappa32 = h.kappa32;
+  } else if (h.eps) {
+    L.epsr32 = nullptr;   // build_dict_dev rejects a level without its FP32 bounds
+  }
   if (h.kind == LK_KRON) {
     L.B = d->Bf;
     L.C = d->Cf;
@@ -513,13 +536,15 @@ int ensure_rung64(lasso_dict* d) {
   h = d->exact;               // shares the FP32 data and vectors of the exact level
   h.owns_data = false;
   h.kind = LK_F32D;
-  h.epsr32[0] = h.epsr32[1] = nullptr;
+  for (auto& e : h.epsr32) e = nullptr;
+  h.kappa32 = nullptr;
   return LASSO_OK;
 }
 
 static bool dict_trace() { return getenv("LASSO_TRACE_STEPS") != nullptr; }
 
-int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order) {
+int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order,
+                   bool tc_levels) {
   if (dict_trace()) fprintf(stderr, "[lasso trace] build_dict_dev: enter\n");
   memset(out, 0, sizeof(*out));
   out->N = (int)d->N;
@@ -554,7 +579,7 @@ int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<con
   out->n_levels = (int)lv.size();
   const bool vt_double = final_fp64 || d->exact_kind == LK_F64;
   for (size_t i = 0; i < lv.size(); ++i) {
-    out->lv[i] = make_level_dev(d, *lv[i], vt_double);
+    out->lv[i] = make_level_dev(d, *lv[i], vt_double, tc_levels);
     if (!out->lv[i].epsr32) return LASSO_ERR_CUDA;
   }
   if (order) *order = lv;
@@ -897,8 +922,8 @@ extern "C" void lasso_dict_destroy(lasso_dict* d) {
   cudaFree(d->anorm);
   cudaFree(d->anorm32);
   if (d->rung64.kind >= 0) {
-    cudaFree(d->rung64.epsr32[0]);
-    cudaFree(d->rung64.epsr32[1]);
+    for (auto* e : d->rung64.epsr32) cudaFree(e);
+    cudaFree(d->rung64.kappa32);
   }
   delete d;
 }

@@ -18,7 +18,8 @@ struct HostLevel {
   double* eps = nullptr;
   double* kappa = nullptr;
   float* atnorm = nullptr;
-  float* epsr32[2] = {nullptr, nullptr};   // per iterate precision (FP32, FP64)
+  float* epsr32[4] = {nullptr, nullptr, nullptr, nullptr};   // per (iterate precision, tensor cores)
+  float* kappa32 = nullptr;
   float* dscale = nullptr;     // Kronecker d_j as FP32
   double u = U32, gam_corr = 0.0, gam_res = 0.0, rc = 1.0;
   bool rc_set = false;
@@ -53,9 +54,11 @@ struct lasso_dict {
 namespace lasso {
 
 // Level descriptor for kernels.  vt_double: the solve iterates in FP64 (affects the roundings).
-LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double = false);
-// All levels of a solve, coarsest first, exact (or the FP64 rung) last.
-int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order);
+LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double = false, bool tc = false);
+// All levels of a solve, coarsest first, exact (or the FP64 rung) last.  tc_levels: run the
+// batched BF16 / FP8 correlations on the tensor cores.
+int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order,
+                   bool tc_levels = false);
 int ensure_rung64(lasso_dict* d);
 int dict_prepare(lasso_dict* d, double L_override);
 

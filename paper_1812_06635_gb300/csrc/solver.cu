@@ -15,6 +15,7 @@
 
 #include "dict.cuh"
 #include "kernels.cuh"
+#include "tc_gemm.cuh"
 
 namespace lasso {
 
@@ -54,6 +55,9 @@ struct Workspace {
   float* AZ = nullptr;               // B x ldN
   float* Xd = nullptr;               // B x K
   float* Tk = nullptr;               // B x R x max(K1 N2, N1 K2)
+  void* rq[MAX_LEVELS] = {nullptr};  // tensor-core levels: quantised residuals (B x ldN)
+  float* rsig[MAX_LEVELS] = {nullptr};
+  int* tc_err = nullptr;
   int32_t* h_counters = nullptr;     // pinned
   cudaStream_t stream = nullptr;     // used when the caller passes the legacy default stream
   int nrb = 0, nch = 0;
@@ -65,6 +69,11 @@ void free_ws(Workspace* w) {
                   w->mask, w->cand_idx, w->cand_val, w->offsets2, w->part_full,
                   w->part_res, w->part_corr, w->offsets, w->counters, w->alg_bytes, w->st, w->Gfull, w->AZ, w->Xd, w->Tk};
   for (void* p : ptrs) cudaFree(p);
+  for (int l = 0; l < MAX_LEVELS; ++l) {
+    cudaFree(w->rq[l]);
+    cudaFree(w->rsig[l]);
+  }
+  cudaFree(w->tc_err);
   cudaFreeHost(w->h_counters);
   if (w->stream) cudaStreamDestroy(w->stream);
   delete w;
@@ -131,6 +140,7 @@ static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
     rc |= ws_alloc((void**)&w->Xd, BK * 4);
     rc |= ws_alloc((void**)&w->Tk, tk * 4);
   }
+  rc |= ws_alloc((void**)&w->tc_err, 16);
   if (cudaHostAlloc((void**)&w->h_counters, 64, cudaHostAllocDefault) != cudaSuccess) rc |= 1;
   if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) rc |= 1;
   if (rc) {
@@ -525,7 +535,9 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
     const float inv_Lf = (float)inv_L, thr_f = (float)thr, beta_f = (float)s.beta;
     double m1 = 0.0, m2 = 0.0;
     float m1f = 0.f, m2f = 0.f;
-    const bool pair = MODE == CORR_PASS && (L.kind == LK_F32 || L.kind == LK_BF16 || L.kind == LK_FP8);
+    const bool pair = MODE == CORR_PASS && !L.tc && (L.kind == LK_F32 || L.kind == LK_BF16 || L.kind == LK_FP8);
+    const bool from_full = L.kind == LK_KRON || (MODE == CORR_PASS && L.tc);
+    const float dq_f = from_full && L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
     constexpr int NW = CORR_THREADS / 32;
     for (int base = p0 + wid; base < p1; base += (pair ? 2 : 1) * NW) {
       double gg[2] = {0.0, 0.0};
@@ -539,7 +551,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
         warp_atom_dot2_fast<VT>(L, jj[0], jj[1], ldN, src, lane, f0, f1);
         gg[0] = f0;
         gg[1] = f1;
-      } else if (L.kind == LK_KRON) {
+      } else if (from_full) {
         gg[0] = (double)a.Gfull[(int64_t)b * a.K + jj[0]];
       } else if (MODE == CORR_PASS) {
         gg[0] = warp_atom_dot_fast<VT>(L, jj[0], ldN, src, lane);
@@ -557,7 +569,8 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
           // eps_j + gam kappa_j (FP32, rounded up); the INIT / CERT passes use the tight bound
           const float er = MODE == CORR_PASS ? L.epsr32[j]
                                              : __double2float_ru(L.eps[j] + gam * L.kappa[j]);
-          const float ub = __fmaf_ru(er, nrho_f, __fmul_ru(ag, ga_fac));
+          float ub = __fmaf_ru(er, nrho_f, __fmul_ru(ag, ga_fac));
+          if (dq_f > 0.f) ub = __fmaf_ru(L.kappa32[j], dq_f, ub);
           if (MODE == CORR_PASS) {
             m1f = fmaxf(m1f, ub);
             m2f = fmaxf(m2f, ag);
@@ -582,7 +595,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
           const double g = gg[q];
           const double ga = fabs(g) * (1.0 + 3.0 * ug);
           const double epsr = L.eps[j] + gam * L.kappa[j];
-          m1 = fmax(m1, ga + epsr * nrho);
+          m1 = fmax(m1, ga + epsr * nrho + (dq_f > 0.f ? L.kappa[j] * s.dq * 1.001 : 0.0));
           m2 = fmax(m2, fabs(g));
           if (MODE == CORR_INIT) {
             if (a.c0ub) a.c0ub[(int64_t)b * a.K + j] = __double2float_ru(ga + epsr * nrho);
@@ -619,7 +632,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
       double* pc = a.part_corr + ((int64_t)b * a.nch + chunk) * 2;
       pc[0] = t1;
       pc[1] = t2;
-      if (MODE == CORR_PASS && a.alg_bytes && L.kind != LK_KRON) {
+      if (MODE == CORR_PASS && a.alg_bytes && L.kind != LK_KRON && !L.tc) {
         // preserved atoms of the chunk (rows of A~, index, x and z read and written, g written),
         // plus rho once per signal
         const double vs = (double)sizeof(VT);
@@ -863,20 +876,25 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
   const float c_eps_f = __double2float_ru(c_eps), Rs_f = __double2float_ru(Rs);
   const float inv_lam_f = __double2float_ru(inv_lam), thr_f = __double2float_rd(thr);
   const float abs_st_f = (float)abs_st, Rt_f = (float)Rt;
+  const float c_dq_f = L.tc ? __double2float_ru(abs_sp * s.dq * 1.001) : 0.f;
   auto keep_of = [&](int pos, int64_t j, double& mu_out) -> bool {
     if (!screen) return true;
     if constexpr (sizeof(VT) == 4) {
       float mu;
-      if (gap_rule)
+      if (gap_rule) {
         mu = __fadd_ru(__fmaf_ru(L.epsr32[j], c_eps_f, __fmul_ru(__fmul_ru(abs_sp_f, fabsf((float)G[pos])), gfac_f)),
                        __fmul_ru(Rs_f, anorm32[j]));
+        if (c_dq_f > 0.f) mu = __fmaf_ru(L.kappa32[j], c_dq_f, mu);
+      }
       else
         mu = __fadd_ru(__fmul_ru(c0[j], inv_lam_f), __fmul_ru(Rs_f, anorm32[j]));
       mu_out = mu;
       return mu >= thr_f;
     } else {
       double mu;
-      if (gap_rule) mu = abs_sp * fabs((double)G[pos]) * gfac + (L.eps[j] + L.gam_corr * L.kappa[j]) * c_eps + Rs * anorm[j];
+      if (gap_rule)
+        mu = abs_sp * fabs((double)G[pos]) * gfac + (L.eps[j] + L.gam_corr * L.kappa[j]) * c_eps + Rs * anorm[j] +
+             (L.tc ? L.kappa[j] * abs_sp * s.dq * 1.001 : 0.0);
       else mu = (double)c0[j] * inv_lam + Rs * anorm[j];
       mu_out = mu * (1.0 + 4.0 * U64);
       return mu >= thr;
@@ -1124,6 +1142,67 @@ __global__ void k_full_finish(PassArgs<VT> a) {
   }
 }
 
+// ------------------------------------------------------------------ tensor-core operand
+
+// Quantise rho^ of the signals on a tensor-core level (BF16, or E4M3 with the per-signal scale
+// sigma = max |rho| / 448) and record dq = ||rho^ - sigma r^|| exactly: the correlation of the
+// quantised operand differs from a~_j^T rho^ by at most ||a~_j|| dq, which the bounds add.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_quant_rho(PassArgs<VT> a, int lvl, int fp8) {
+  const int b = blockIdx.x;
+  __shared__ int s_go;
+  __shared__ float s_max[8];
+  __shared__ double s_sum[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_go = !a.st[b].done && a.st[b].level == lvl;
+  __syncthreads();
+  if (!s_go) return;
+  const LevelDev& L = a.dd.lv[lvl];
+  const VT* rho = a.Rho + (int64_t)b * a.ldN;
+  const int N = a.dd.N;
+  float m = 0.f;
+  for (int n = threadIdx.x; n < N; n += 256) m = fmaxf(m, fabsf((float)rho[n]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) s_max[wid] = m;
+  __syncthreads();
+  float mx = 0.f;
+  for (int w = 0; w < 8; ++w) mx = fmaxf(mx, s_max[w]);
+  const float sg = fp8 ? (mx > 0.f ? mx / 448.f : 1.f) : 1.f;
+  double dq2 = 0.0;
+  if (fp8) {
+    uint8_t* out = reinterpret_cast<uint8_t*>(L.rq) + (int64_t)b * a.ldN;
+    for (int n = threadIdx.x; n < a.ldN; n += 256) {
+      const double r = n < N ? (double)rho[n] : 0.0;
+      const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fdiv_rn((float)r, sg), __NV_SATFINITE, __NV_E4M3);
+      out[n] = q;
+      __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+      const double e = r - (double)__half2float(__half(hr)) * (double)sg;
+      dq2 = fma(e, e, dq2);
+    }
+  } else {
+    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(L.rq) + (int64_t)b * a.ldN;
+    for (int n = threadIdx.x; n < a.ldN; n += 256) {
+      const double r = n < N ? (double)rho[n] : 0.0;
+      const __nv_bfloat16 q = __float2bfloat16_rn((float)r);
+      out[n] = q;
+      const double e = r - (double)__bfloat162float(q);
+      dq2 = fma(e, e, dq2);
+    }
+  }
+  dq2 = warp_sum(dq2);
+  if (lane == 0) s_sum[wid] = dq2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += s_sum[w];
+    a.st[b].dq = sqrt(t) * (1.0 + 1e-12);
+    L.rsig[b] = sg;
+    // algorithmic work of the batched correlation of this signal: 2 N K flops
+    if (a.alg_bytes) atomicAdd(&a.alg_bytes[5], 2.0 * (double)a.dd.N * (double)a.K);
+  }
+}
+
 // ------------------------------------------------------------------ Kronecker levels
 
 // Batched FP32 GEMM tile: C[bz](m, n) (+)= sum_{r < R} sum_k A(bz, r, m, k) B(bz, r, k, n).
@@ -1355,11 +1434,19 @@ struct SolveIO {
 
 // Events of one pass (profile mode): before residual stage, before correlation, before
 // screening, before schedule, end; Kronecker stages are timed between their own events.
-constexpr int PASS_EVENTS = 7;
+constexpr int PASS_EVENTS = 9;
+
+// A tensor-core level of the current solve: its operand tensor maps and scales.
+struct TcJob {
+  int lvl, fp8;
+  TcOperands ops;
+  const float* scale;
+  float* rsig;
+};
 
 template <typename VT>
 static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, int corr_grid, size_t corr_smem,
-                        cudaEvent_t* ev) {
+                        cudaEvent_t* ev, const std::vector<TcJob>& tc, int* tc_err) {
   const int B = pa.sp.B;
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   if (has_kron) {
@@ -1397,6 +1484,12 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
     k_kron_gemm<VT, KS_T><<<dim3(tiles(N2), tiles(K1), B * Rmax), 256, 0, st>>>(pa);
     k_kron_gemm<VT, KS_G><<<dim3(tiles(K2), tiles(K1), B), 256, 0, st>>>(pa);
   }
+  if (ev) cudaEventRecordWithFlags(ev[7], st, cudaEventRecordExternal);
+  for (const TcJob& j : tc) {
+    k_quant_rho<VT><<<B, 256, 0, st>>>(pa, j.lvl, j.fp8);
+    tc_launch_corr(j.ops, pa.K, B, pa.ldN, j.scale, j.rsig, pa.st, j.lvl, pa.Gfull, tc_err, st);
+  }
+  if (ev) cudaEventRecordWithFlags(ev[8], st, cudaEventRecordExternal);
   if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
   k_corr<VT, CORR_PASS><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
@@ -1411,7 +1504,9 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
 }
 
-static int pass_launches(bool has_kron, bool full_gap) { return (has_kron ? 9 : 4) + (full_gap ? 3 : 0); }
+static int pass_launches(bool has_kron, bool full_gap, int n_tc) {
+  return (has_kron ? 9 : 4) + (full_gap ? 3 : 0) + 2 * n_tc;
+}
 
 template <typename VT>
 static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats* stats) {
@@ -1423,8 +1518,40 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   PassArgs<VT> pa;
   memset(&pa, 0, sizeof(pa));
   std::vector<const HostLevel*> order;
-  int rc = build_dict_dev(d, o.final_fp64 != 0, &pa.dd, &order);
+  bool want_tc = o.tensor_cores && B >= TC_BN && d->K >= TC_BM;
+  if (want_tc) {
+    bool any = false;
+    for (auto& h : d->approx) any |= h.kind == LK_BF16 || h.kind == LK_FP8;
+    want_tc = any;
+  }
+  int rc = build_dict_dev(d, o.final_fp64 != 0, &pa.dd, &order, want_tc);
   if (rc) return rc;
+  std::vector<TcJob> tc_jobs;
+  for (int l = 0; l < pa.dd.n_levels; ++l) {
+    LevelDev& L = pa.dd.lv[l];
+    if (!L.tc) continue;
+    const int fp8 = L.kind == LK_FP8;
+    const size_t bytes = (size_t)w->B * d->ldN * (fp8 ? 1 : 2);
+    if (!w->rq[l]) {
+      if (ws_alloc(&w->rq[l], (size_t)w->B * d->ldN * 2) || ws_alloc((void**)&w->rsig[l], (size_t)w->B * 4))
+        return LASSO_ERR_NOMEM;
+      LASSO_CUDA_TRY(cudaMemset(w->rq[l], 0, (size_t)w->B * d->ldN * 2));
+    }
+    (void)bytes;
+    L.rq = w->rq[l];
+    L.rsig = w->rsig[l];
+    TcJob job;
+    job.lvl = l;
+    job.fp8 = fp8;
+    job.scale = fp8 ? L.scale : nullptr;
+    job.rsig = fp8 ? L.rsig : nullptr;
+    rc = tc_make_operands(L.data, d->K, L.rq, B, d->ldN, fp8, &job.ops);
+    if (rc) return rc;
+    tc_jobs.push_back(job);
+  }
+  if (!tc_jobs.empty() && !w->Gfull) {
+    if (ws_alloc((void**)&w->Gfull, (size_t)w->B * d->K * 4)) return LASSO_ERR_NOMEM;
+  }
   bool has_kron = false;
   int rmax = 0;
   for (int l = 0; l < pa.dd.n_levels; ++l) {
@@ -1470,6 +1597,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   k_schedule<VT><<<1, 1024, 0, st>>>(pa);
   LASSO_CUDA_TRY(cudaGetLastError());
   LASSO_CUDA_TRY(cudaMemsetAsync(w->alg_bytes, 0, 16 * sizeof(double), st));
+  LASSO_CUDA_TRY(cudaMemsetAsync(w->tc_err, 0, 4, st));
   // capture k passes
   const int k = std::max(1, o.passes_per_sync);
   cudaGraph_t graph = nullptr;
@@ -1482,7 +1610,8 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   }
   double kms[6] = {0, 0, 0, 0, 0, 0};
   for (int i = 0; i < k; ++i)
-    launch_pass<VT>(pa, st, has_kron, corr_grid, corr_smem, o.profile ? &evs[(size_t)i * PASS_EVENTS] : nullptr);
+    launch_pass<VT>(pa, st, has_kron, corr_grid, corr_smem, o.profile ? &evs[(size_t)i * PASS_EVENTS] : nullptr,
+                    tc_jobs, w->tc_err);
   cudaError_t ce = cudaStreamEndCapture(st, &graph);
   if (ce != cudaSuccess) {
     set_last_error(cudaGetErrorString(ce), __FILE__, __LINE__);
@@ -1511,10 +1640,11 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
         float t;
         if (cudaEventElapsedTime(&t, e[0], e[1]) == cudaSuccess) kms[4] += t;
         if (cudaEventElapsedTime(&t, e[1], e[2]) == cudaSuccess) kms[0] += t;
-        if (cudaEventElapsedTime(&t, e[2], e[3]) == cudaSuccess) kms[4] += t;
+        if (cudaEventElapsedTime(&t, e[2], e[7]) == cudaSuccess) kms[4] += t;
         if (cudaEventElapsedTime(&t, e[3], e[4]) == cudaSuccess) kms[1] += t;
         if (cudaEventElapsedTime(&t, e[4], e[5]) == cudaSuccess) kms[2] += t;
         if (cudaEventElapsedTime(&t, e[5], e[6]) == cudaSuccess) kms[3] += t;
+        if (cudaEventElapsedTime(&t, e[7], e[8]) == cudaSuccess) kms[5] += t;
       }
       cudaGetLastError();   // a failed timing query must not leave a sticky error behind
     }
@@ -1542,7 +1672,15 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   double hbytes[16] = {0};
   LASSO_CUDA_TRY(cudaMemcpyAsync(hbytes, w->alg_bytes, sizeof(hbytes), cudaMemcpyDeviceToHost, st));
   LASSO_CUDA_TRY(cudaStreamSynchronize(st));
-  int64_t launches = 6 + replays * (int64_t)k * pass_launches(has_kron, pa.sp.full_gap != 0);
+  int64_t launches = 6 + replays * (int64_t)k * pass_launches(has_kron, pa.sp.full_gap != 0, (int)tc_jobs.size());
+  {
+    int herr = 0;
+    LASSO_CUDA_TRY(cudaMemcpy(&herr, w->tc_err, 4, cudaMemcpyDeviceToHost));
+    if (herr) {
+      set_last_error("tensor-core pipeline wait expired", __FILE__, __LINE__);
+      return LASSO_ERR_TIMEOUT;
+    }
+  }
   if (o.certify_full && result == LASSO_OK) {
     // certificate over every atom (offsets: K / CHUNK items per signal)
     std::vector<int32_t> offs(B + 1);
@@ -1570,7 +1708,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     stats->lambda_max = hs[0].lam_max_lb;
     stats->lambda = hs[0].lam;
     stats->launches = launches;
-    const int per_pass[6] = {1, 1, pa.sp.full_gap ? 4 : 1, 1, has_kron ? 5 : 0, 0};
+    const int per_pass[6] = {1, 1, pa.sp.full_gap ? 4 : 1, 1, has_kron ? 5 : 0, 2 * (int)tc_jobs.size()};
     for (int q = 0; q < 6; ++q) {
       stats->kernel_launches[q] = replays * (int64_t)k * per_pass[q];
       stats->kernel_ms[q] = kms[q];

@@ -1,0 +1,424 @@
+// Tensor-core correlation of a batch with an approximate dictionary (BF16 or per-atom scaled
+// E4M3): G[b][j] = scale_j sigma_b sum_n q_jn r^_bn, on the 5th-generation tensor cores.
+//
+// One CTA computes a 128-atom x 256-signal tile: warp 0 streams 128-byte K-slices of both
+// operands into a 4-stage shared-memory ring with TMA (128B swizzle), warp 1 issues
+// tcgen05.mma (M = 128, N = 256, FP32 accumulators in TMEM) and commits each stage back to the
+// producer, warps 2-5 read the accumulators with tcgen05.ld and scale/store them.  Tiles whose
+// 256 signals are all on other ladder levels (or finished) exit before allocating anything.
+// Every mbarrier wait is bounded: on expiry the CTA records an error and still frees its TMEM.
+//
+// Paper: the correlation A~^T rho of the proximal update (eq:ISTA_update) with the approximate
+// dictionaries of Section III; here batched over signals, which makes it a dense contraction.
+#include <cstring>
+
+#include <cudaTypedefs.h>
+
+#include "tc_gemm.cuh"
+
+namespace lasso {
+
+constexpr uint32_t TC_WAIT_POLLS = 1u << 22;   // bounded mbarrier waits (seconds, never forever)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (uint32_t i = 0; i < TC_WAIT_POLLS; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// UMMA instruction descriptor: FP32 accumulation, A and B K-major, M x N tile.
+// ab_format: 1 = BF16 (kind::f16), 0 = E4M3 (kind::f8f6f4).
+__host__ __device__ constexpr uint32_t umma_idesc(uint32_t ab_format, uint32_t M, uint32_t N) {
+  return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle layout: rows of
+// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused by swizzled K-major layouts)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+template <int FP8>
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  if constexpr (FP8) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int FP8>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb, int64_t K, int64_t B,
+          int nkb, const float* __restrict__ scale, const float* __restrict__ sigma, const SigState* __restrict__ st,
+          int lvl, float* __restrict__ Gfull, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t tc_smem[];
+  __shared__ int s_active, s_fail;
+  __shared__ uint8_t s_on[TC_BN];
+  __shared__ float s_sigma[TC_BN];
+  __shared__ uint32_t s_tmem;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = base;                                    // TC_STAGES x 16 KB
+  uint8_t* sB = base + TC_STAGES * TC_BM * 128;          // TC_STAGES x 32 KB
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_BN * 128);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* accum = empty + TC_STAGES;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
+  const int64_t n0 = (int64_t)blockIdx.y * TC_BN;
+
+  // ---- which signals of the tile are on this level (uniform early exit)
+  if (threadIdx.x == 0) {
+    s_active = 0;
+    s_fail = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < TC_BN; i += TC_THREADS) {
+    const int64_t b = n0 + i;
+    uint8_t on = 0;
+    float sg = 0.f;
+    if (b < B && !st[b].done && st[b].level == lvl) {
+      on = 1;
+      sg = sigma ? sigma[b] : 1.f;
+      atomicOr(&s_active, 1);
+    }
+    s_on[i] = on;
+    s_sigma[i] = sg;
+  }
+  __syncthreads();
+  if (!s_active) return;
+
+  // ---- barriers and tensor memory
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  constexpr int KB_ELEMS = FP8 ? 128 : 64;   // elements per 128-byte K-slice
+
+  if (warp == 0) {
+    // ---- TMA producer
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+        if (kb >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+          s_fail = 1;
+          break;
+        }
+        mbar_expect_tx(&full[s], (uint32_t)(TC_BM + TC_BN) * 128u);
+        tma_load_2d(&tma, &full[s], sA + s * TC_BM * 128, kb * KB_ELEMS, (int)m0);
+        tma_load_2d(&tmb, &full[s], sB + s * TC_BN * 128, kb * KB_ELEMS, (int)n0);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc(FP8 ? 0u : 1u, TC_BM, TC_BN);
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+        if (!mbar_wait(&full[s], ph)) {
+          s_fail = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t ad = umma_sdesc(smem_u32(sA + s * TC_BM * 128));
+        const uint64_t bd = umma_sdesc(smem_u32(sB + s * TC_BN * 128));
+#pragma unroll
+        for (int k = 0; k < 4; ++k)   // four 32-byte K-steps per 128-byte slice
+          umma<FP8>(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+        umma_commit(&empty[s]);
+      }
+      umma_commit(accum);   // arrives once every MMA issued above has completed
+    }
+  } else {
+    // ---- epilogue: TMEM lane quarter (warp % 4) holds atoms m0 + 32 q .. + 31
+    const int q = warp & 3;
+    const int64_t row = m0 + q * 32 + lane;
+    const bool ok = mbar_wait(accum, 0);
+    if (!ok) s_fail = 1;
+    tc_fence_after();
+    const float sc = row < K ? (scale ? scale[row] : 1.f) : 0.f;
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+      if (ok && row < K) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int64_t b = n0 + c0 + i;
+          if (s_on[c0 + i]) Gfull[b * K + row] = __uint_as_float(r[i]) * sc * s_sigma[c0 + i];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+  }
+  if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+}
+
+// ------------------------------------------------------------------ host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static int encode_2d(CUtensorMap* map, const void* ptr, int64_t rows, int64_t ld, int fp8, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_last_error("cuTensorMapEncodeTiled unavailable", __FILE__, __LINE__);
+    return LASSO_ERR_CUDA;
+  }
+  const int es = fp8 ? 1 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr),
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_error("cuTensorMapEncodeTiled failed", __FILE__, __LINE__);
+    return LASSO_ERR_CUDA;
+  }
+  return LASSO_OK;
+}
+
+int tc_make_operands(const void* level_data, int64_t K, const void* rq, int64_t B, int64_t ldN, int fp8,
+                     TcOperands* out) {
+  if ((ldN * (fp8 ? 1 : 2)) % 16 != 0 || (reinterpret_cast<uintptr_t>(level_data) & 15) ||
+      (reinterpret_cast<uintptr_t>(rq) & 15))
+    return LASSO_ERR_INVALID_ARG;
+  out->fp8 = fp8;
+  int rc = encode_2d(&out->a, level_data, K, ldN, fp8, TC_BM);
+  if (rc) return rc;
+  return encode_2d(&out->b, rq, B, ldN, fp8, TC_BN);
+}
+
+void tc_launch_corr(const TcOperands& ops, int64_t K, int64_t B, int64_t ldN, const float* scale,
+                    const float* sigma, const SigState* st, int lvl, float* Gfull, int* err, cudaStream_t stream) {
+  static bool attr[2] = {false, false};
+  const int es = ops.fp8 ? 1 : 2;
+  const int nkb = (int)((ldN * es + 127) / 128);   // 128-byte K-slices (TMA zero-fills the tail)
+  const dim3 grid((unsigned)((K + TC_BM - 1) / TC_BM), (unsigned)((B + TC_BN - 1) / TC_BN));
+  if (ops.fp8) {
+    if (!attr[1]) {
+      cudaFuncSetAttribute(k_tc_corr<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+      attr[1] = true;
+    }
+    k_tc_corr<1><<<grid, TC_THREADS, TC_SMEM, stream>>>(ops.a, ops.b, K, B, nkb, scale, sigma, st, lvl, Gfull, err);
+  } else {
+    if (!attr[0]) {
+      cudaFuncSetAttribute(k_tc_corr<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+      attr[0] = true;
+    }
+    k_tc_corr<0><<<grid, TC_THREADS, TC_SMEM, stream>>>(ops.a, ops.b, K, B, nkb, scale, sigma, st, lvl, Gfull, err);
+  }
+}
+
+// ------------------------------------------------------------------ self-test
+
+__device__ __forceinline__ uint32_t tc_hash(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return (uint32_t)x;
+}
+
+// Operands with a wide dynamic range: |v| = 2^e (1 + m / 8), e in [-6, 5] (E4M3 exact) or BF16
+// values of a uniform grid; `positive` makes every product the same sign (worst accumulation).
+__global__ void k_tc_fill(uint8_t* __restrict__ dst, int64_t rows, int64_t ld, int64_t N, int fp8, int positive,
+                          uint64_t seed) {
+  const int64_t total = rows * ld;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = t % ld;
+    const uint32_t h = tc_hash(seed * 0x9E3779B97F4A7C15ull + (uint64_t)t);
+    float v = 0.f;
+    if (n < N) {
+      const int e = (int)(h % 12) - 6;
+      const int m = (int)((h >> 8) % 8);
+      v = ldexpf(1.f + m / 8.f, e);
+      if (!positive && ((h >> 16) & 1)) v = -v;
+    }
+    if (fp8) dst[t] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    else reinterpret_cast<__nv_bfloat16*>(dst)[t] = __float2bfloat16_rn(v);
+  }
+}
+
+__device__ __forceinline__ double tc_val(const uint8_t* p, int64_t idx, int fp8) {
+  if (fp8) {
+    __half_raw hr = __nv_cvt_fp8_to_halfraw(p[idx], __NV_E4M3);
+    return (double)__half2float(__half(hr));
+  }
+  return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[idx]);
+}
+
+// FP64 reference and error statistics: err / sum|a r| and err / (gamma_n(u_tc) sum|a r|).
+__global__ void k_tc_check(const uint8_t* __restrict__ A, const uint8_t* __restrict__ R, const float* __restrict__ G,
+                           int64_t K, int64_t B, int64_t ld, int fp8, double gam, unsigned long long* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= K * B) return;
+  const int64_t j = t % K, b = t / K;
+  double s = 0.0, sa = 0.0;
+  for (int64_t n = 0; n < ld; ++n) {
+    const double p = tc_val(A, j * ld + n, fp8) * tc_val(R, b * ld + n, fp8);
+    s += p;
+    sa += fabs(p);
+  }
+  const double err = fabs((double)G[b * K + j] - s);
+  const double rel = sa > 0.0 ? err / sa : 0.0;
+  const double ratio = sa > 0.0 ? err / (gam * sa) : 0.0;
+  atomicMax(&out[0], __double_as_longlong(rel));
+  atomicMax(&out[1], __double_as_longlong(ratio));
+}
+
+int tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel, double* max_ratio) {
+  const int64_t ld = round_up(N, 16);
+  const int es = fp8 ? 1 : 2;
+  uint8_t *A = nullptr, *R = nullptr;
+  float* G = nullptr;
+  SigState* st = nullptr;
+  int* err = nullptr;
+  unsigned long long* out = nullptr;
+  int rc = LASSO_OK;
+  if (cudaMalloc(&A, K * ld * es) != cudaSuccess || cudaMalloc(&R, B * ld * es) != cudaSuccess ||
+      cudaMalloc(&G, K * B * 4) != cudaSuccess || cudaMalloc(&st, B * sizeof(SigState)) != cudaSuccess ||
+      cudaMalloc(&err, 4) != cudaSuccess || cudaMalloc(&out, 16) != cudaSuccess)
+    rc = LASSO_ERR_NOMEM;
+  double rel = 0.0, ratio = 0.0;
+  for (int positive = 0; positive < 2 && rc == LASSO_OK; ++positive) {
+    cudaMemset(st, 0, B * sizeof(SigState));   // every signal on level 0, not done
+    cudaMemset(err, 0, 4);
+    cudaMemset(out, 0, 16);
+    cudaMemset(G, 0, K * B * 4);
+    k_tc_fill<<<1024, 256>>>(A, K, ld, N, fp8, positive, 11 + positive);
+    k_tc_fill<<<1024, 256>>>(R, B, ld, N, fp8, positive, 29 + positive);
+    TcOperands ops;
+    rc = tc_make_operands(A, K, R, B, ld, fp8, &ops);
+    if (rc) break;
+    tc_launch_corr(ops, K, B, ld, nullptr, nullptr, st, 0, G, err, 0);
+    const int nk = (int)(ld / (fp8 ? 32 : 16));
+    const double gam = gamma_n((double)ld + nk, fp8 ? TC_U_FP8 : TC_U_BF16);
+    k_tc_check<<<(unsigned)((K * B + 255) / 256), 256>>>(A, R, G, K, B, ld, fp8, gam, out);
+    int herr = 0;
+    unsigned long long h[2] = {0, 0};
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(h, out, 16, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      set_last_error(cudaGetErrorString(cudaGetLastError()), __FILE__, __LINE__);
+      rc = LASSO_ERR_CUDA;
+      break;
+    }
+    if (herr) {
+      rc = LASSO_ERR_TIMEOUT;
+      break;
+    }
+    double r0, r1;
+    memcpy(&r0, &h[0], 8);
+    memcpy(&r1, &h[1], 8);
+    rel = fmax(rel, r0);
+    ratio = fmax(ratio, r1);
+  }
+  cudaFree(A);
+  cudaFree(R);
+  cudaFree(G);
+  cudaFree(st);
+  cudaFree(err);
+  cudaFree(out);
+  if (max_rel) *max_rel = rel;
+  if (max_ratio) *max_ratio = ratio;
+  return rc;
+}
+
+}  // namespace lasso
+
+extern "C" int lasso_tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel_err,
+                                 double* max_err_over_bound) {
+  if (K <= 0 || N <= 0 || B <= 0 || K * B > (int64_t)1 << 28) return LASSO_ERR_INVALID_ARG;
+  return lasso::tc_selftest(fp8 ? 1 : 0, K, N, B, max_rel_err, max_err_over_bound);
+}

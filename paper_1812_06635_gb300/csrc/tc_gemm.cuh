@@ -1,0 +1,42 @@
+// Tensor-core correlation G = A~ R^^T for the batched BF16 / FP8 levels (tcgen05 + TMA + TMEM).
+#pragma once
+
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace lasso {
+
+constexpr int TC_BM = 128;        // atoms per tile (TMEM lanes)
+constexpr int TC_BN = 256;        // signals per tile (TMEM columns, FP32 accumulators)
+constexpr int TC_STAGES = 4;      // TMA ring depth (48 KB per stage)
+constexpr int TC_THREADS = 192;   // warp 0: TMA producer, warp 1: MMA issuer, warps 2-5: epilogue
+constexpr int TC_SMEM = TC_STAGES * (TC_BM + TC_BN) * 128 + 1024 + 256;
+
+// Rounding model of the tensor-core accumulation (products of BF16 / E4M3 operands are exact in
+// FP32; the sum of n products is taken as an FP32 chain with unit roundoff u_tc, no better than
+// 2^-22 for BF16 and 2^-19 for E4M3 inputs).  tests/test_gpu_tc.py checks the observed error
+// against this bound on adversarial and random inputs.
+constexpr double TC_U_BF16 = 2.384185791015625e-07;   // 2^-22
+constexpr double TC_U_FP8 = 1.9073486328125e-06;      // 2^-19
+
+struct TcOperands {
+  CUtensorMap a;          // dictionary level: K rows (atoms) x ldN, K-major
+  CUtensorMap b;          // quantised residuals: B rows (signals) x ldN, K-major
+  int fp8;                // 1: kind::f8f6f4 E4M3, 0: kind::f16 BF16
+};
+
+// Encode the two tensor maps (host).  Returns LASSO_OK or an error status.
+int tc_make_operands(const void* level_data, int64_t K, const void* rq, int64_t B, int64_t ldN, int fp8,
+                     TcOperands* out);
+
+// Gfull[b][j] = scale_j * sigma_b * sum_n q_jn r^_bn for the signals b at ladder level `lvl`
+// (tiles with no such signal exit at once).  err: set to 1 if a pipeline wait gave up.
+void tc_launch_corr(const TcOperands& ops, int64_t K, int64_t B, int64_t ldN, const float* scale,
+                    const float* sigma, const SigState* st, int lvl, float* Gfull, int* err, cudaStream_t stream);
+
+// Self-test: random K x N operands and B signals through the tensor-core GEMM, compared with an
+// FP64 evaluation of the same products; reports the largest error relative to sum |a_i r_i|.
+int tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel, double* max_abs_bound_ratio);
+
+}  // namespace lasso
