@@ -51,6 +51,25 @@ def _dist():
     return rank, world, local
 
 
+def shard_first(rank, signals_per_rank):
+    """First global signal index of a rank's shard: ranks solve disjoint, equally sized slices of
+    one seeded batch (signal i depends only on (seed, i)), so the job needs no data exchange."""
+    return rank * signals_per_rank
+
+
+def job_totals(t_local, solved_local, device):
+    """Whole-job time (max over ranks) and solves (sum over ranks); one rank returns its own."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t_local), int(solved_local)
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(solved_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(n.item()))
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -240,7 +259,7 @@ def run_ours(args):
     pkg.load()
 
     B = args.signals
-    w = S.c3(n_signals=B, first=rank * B)
+    w = S.c3(n_signals=B, first=shard_first(rank, B))
     d = pkg.Dictionary.dense(w.A, dtype="f32").add_level(pkg.LEVEL_FP8).add_level(pkg.LEVEL_BF16).prepare()
     Y = torch.tensor(w.Y, dtype=torch.float32, device=dev)
     ratios = torch.tensor(w.lam_ratio, dtype=torch.float64, device=dev)
@@ -277,15 +296,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    t_local = total_ms / 1e3
-    if world > 1:
-        tt = torch.tensor([t_local, float(solved)], dtype=torch.float64, device=dev)
-        tmax = tt.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t_job, solved_job = float(tmax[0]), int(tt[1])
-    else:
-        t_job, solved_job = t_local, solved
+    t_job, solved_job = job_totals(total_ms / 1e3, solved, dev)
     value = solved_job / t_job
 
     # e2e: the same solve through the C ABI with pinned host buffers, copies included

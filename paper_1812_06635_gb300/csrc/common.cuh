@@ -42,6 +42,7 @@ struct LevelDev {
   const float* atnorm;      // ||a~_j||
   const float* epsr32;      // eps_j + gam_corr kappa_j rounded up to FP32 (bulk bound in FP32 code)
   const float* kappa32;     // kappa_j rounded up to FP32
+  const float* eps32;       // eps_j rounded up to FP32
   int tc;                   // 1: batched correlation on the tensor cores (BF16 / FP8 levels)
   void* rq;                 // tensor-core levels: quantised residuals (B x ld, BF16 or E4M3)
   float* rsig;              // tensor-core levels: per-signal scale of the quantised residual
@@ -52,7 +53,7 @@ struct LevelDev {
   // Rounding of the residual, e_r >= ||rho^ - (y - A~ z)||:
   //   RES_FOLD:  gam_res sum_j |z_j| kappa_j + 2 u ||rho^||
   //   RES_CHAIN: gamma_{nnz+4}(u64) sum_j |z_j| kappa_j + 2 u ||rho^||
-  //   RES_DOT2:  (2 gamma_{2 nnz + 2}(u32)^2 + gam_res) sum_j |z_j| kappa_j + 2 u ||rho^||
+  //   RES_DOT2:  (3 gamma_{2 nnz + 2}(u32)^2 + gam_res) sum_j |z_j| kappa_j + 2 u ||rho^||
   int res_model;
   double gam_res;
   double rc;                // relative complexity (Algorithm 2)
@@ -81,6 +82,11 @@ struct SigState {
   // snapshot of the pass whose reduced certificate met tol, awaiting the full-dictionary check
   double c_rr, c_yr, c_l1, c_epsz, c_kapz, c_m1;
   double dq;                         // ||rho - rho^||: quantisation of the tensor-core operand
+  double rr, yr;                     // ||rho^||^2 and y^T rho^ of the current pass (k_residual)
+  float nrho_ru;                     // ||rho^|| rounded up to FP32
+  float thr_f, beta_f;               // lam / L and the FISTA momentum, as FP32 (update of the pass)
+  float c_nrho_ru;                   // ||rho^|| of the snapshot, rounded up
+  unsigned pm1, pm2;                 // per-pass maxima of the correlation (FP32 bit patterns, >= 0)
   int c_nnz, pending, next_check, pad1;
   int level, n_kept, parity, n_nz, status, done, iters, Kt, n_chunks, pad0;
   int level_passes[MAX_LEVELS];
@@ -93,6 +99,7 @@ __device__ __forceinline__ double residual_bound(const LevelDev& L, double sum_k
 // Knobs of a solve, as kernels see them.
 struct SolveParams {
   double tol, Gamma, tau, L;
+  double inv_L;             // 1 / L
   int algo, rule, screen_every, max_iter;
   int B;
   int chunk;                // atoms per correlation work item (multiple of CORR_CHUNK)
@@ -159,6 +166,17 @@ __device__ __forceinline__ double warp_max(double v) {
   for (int m = 16; m; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
   return v;
 }
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+// Sum of non-negative FP32 terms rounded upward at every step: an upper bound of the exact sum.
+__device__ __forceinline__ float warp_sum_ru(float v) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
 __device__ __forceinline__ int warp_sum_i(int v) {
 #pragma unroll
   for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
@@ -197,7 +215,8 @@ __device__ __forceinline__ double residual_bound(const LevelDev& L, double sum_k
       return gamma_n((double)n_nz + 4.0, U64) * sum_kapz + 2.0 * urho * nrho;
     case RES_DOT2: {
       const double g = gamma_n(2.0 * n_nz + 2.0, U32);
-      return (2.0 * g * g + L.gam_res) * sum_kapz + 2.0 * urho * nrho;
+      // 2 g^2: Dot2 sum; g^2 more for the final FP32 rounding of y - (s + c), u |c| <= u g (...)
+      return (3.0 * g * g + L.gam_res) * sum_kapz + 2.0 * urho * nrho;
     }
     default:
       return L.gam_res * sum_kapz + 2.0 * urho * nrho;

@@ -472,7 +472,10 @@ static void free_level(HostLevel& h) {
   cudaFree(h.kappa);
   cudaFree(h.atnorm);
   for (auto* e : h.epsr32) cudaFree(e);
-  if (h.owns_data || h.kind == LK_KRON) cudaFree(h.kappa32);
+  if (h.owns_data || h.kind == LK_KRON) {
+    cudaFree(h.kappa32);
+    cudaFree(h.eps32);
+  }
   h = HostLevel();
 }
 
@@ -482,6 +485,12 @@ static int ensure_level_f32(const lasso_dict* d, const HostLevel& hc, bool vt_do
   if (!h.kappa32) {
     LASSO_CUDA_TRY(cudaMalloc(&h.kappa32, d->K * sizeof(float)));
     k_round_up_f32<<<grid_for(d->K), 256>>>(h.kappa, nullptr, 0.0, d->K, h.kappa32);
+    LASSO_CUDA_TRY(cudaGetLastError());
+    LASSO_CUDA_TRY(cudaDeviceSynchronize());
+  }
+  if (!h.eps32) {
+    LASSO_CUDA_TRY(cudaMalloc(&h.eps32, d->K * sizeof(float)));
+    k_round_up_f32<<<grid_for(d->K), 256>>>(h.eps, nullptr, 0.0, d->K, h.eps32);
     LASSO_CUDA_TRY(cudaGetLastError());
     LASSO_CUDA_TRY(cudaDeviceSynchronize());
   }
@@ -513,6 +522,7 @@ LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double,
   if (h.eps && ensure_level_f32(d, h, vt_double, tc, L) == LASSO_OK) {
     L.epsr32 = h.epsr32[(vt_double ? 1 : 0) + (tc ? 2 : 0)];
     L.kappa32 = h.kappa32;
+    L.eps32 = h.eps32;
   } else if (h.eps) {
     L.epsr32 = nullptr;   // build_dict_dev rejects a level without its FP32 bounds
   }
@@ -538,6 +548,7 @@ int ensure_rung64(lasso_dict* d) {
   h.kind = LK_F32D;
   for (auto& e : h.epsr32) e = nullptr;
   h.kappa32 = nullptr;
+  h.eps32 = nullptr;
   return LASSO_OK;
 }
 
@@ -924,6 +935,7 @@ extern "C" void lasso_dict_destroy(lasso_dict* d) {
   if (d->rung64.kind >= 0) {
     for (auto* e : d->rung64.epsr32) cudaFree(e);
     cudaFree(d->rung64.kappa32);
+    cudaFree(d->rung64.eps32);
   }
   delete d;
 }

@@ -20,6 +20,7 @@ struct HostLevel {
   float* atnorm = nullptr;
   float* epsr32[4] = {nullptr, nullptr, nullptr, nullptr};   // per (iterate precision, tensor cores)
   float* kappa32 = nullptr;
+  float* eps32 = nullptr;      // eps_j rounded up to FP32
   float* dscale = nullptr;     // Kronecker d_j as FP32
   double u = U32, gam_corr = 0.0, gam_res = 0.0, rc = 1.0;
   bool rc_set = false;

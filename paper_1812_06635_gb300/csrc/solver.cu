@@ -19,7 +19,7 @@
 
 namespace lasso {
 
-constexpr int SCREEN_THREADS = 512;
+constexpr int SCREEN_THREADS = 256;
 constexpr int CORR_THREADS = 256;
 constexpr int RES_ROWS = RES_THREADS * 4;   // rows per residual block
 constexpr int GEMM_T = 64;                  // tile of the Kronecker small GEMMs
@@ -338,142 +338,214 @@ __global__ void k_schedule(PassArgs<VT> a) {
 
 // ------------------------------------------------------------------ residual (dense levels)
 
-// rho^_b = y_b - sum_{j in nz(z_b)} z_bj a~_j over 4 rows per thread, plus ||rho^||^2 and y^T rho^.
+// rho^_b = y_b - sum_{j in nz(z_b)} z_bj a~_j, one block per signal (4 rows per thread per row
+// group), plus ||rho^||^2 and y^T rho^, which the block finishes itself: the pass scalars land in
+// the signal's state (FP64 rr, yr; FP32 ||rho^|| rounded up, lam / L and the FISTA momentum).
+// Float iterates keep every per-row operation in FP32 (FP64 runs at 1/64 of the FP32 rate):
+// compensated (double-float) sums stand in for FP64 accumulators.
 template <typename VT>
 __global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
-  const int b = blockIdx.y;
-  const SigState& s = a.st[b];
-  if (s.done) return;
-  const LevelDev& L = a.dd.lv[s.level];
-  const int r0 = (blockIdx.x * RES_THREADS + threadIdx.x) * 4;
+  const int b = blockIdx.x;
+  SigState* sp = a.st + b;
+  __shared__ int s_live;
+  __shared__ int32_t s_idx[RES_THREADS];
+  __shared__ float s_wf[RES_THREADS];
+  __shared__ double s_wd[RES_THREADS];
+  __shared__ double s_red[4][RES_THREADS / 32];
+  if (threadIdx.x == 0) s_live = !sp->done;
+  __syncthreads();
+  if (!s_live) return;
+  const int lvl = sp->level, nnz = sp->n_nz;
+  const LevelDev& L = a.dd.lv[lvl];
   const VT* y = a.Yw + (int64_t)b * a.ldN;
   VT* rho = a.Rho + (int64_t)b * a.ldN;
-  __shared__ int32_t s_idx[RES_THREADS];
-  __shared__ double s_val[RES_THREADS];
-  __shared__ double s_red[2][RES_THREADS / 32];
-  const bool active = r0 < a.dd.N;
-  const bool writer = r0 < a.ldN;
-  double out[4] = {0.0, 0.0, 0.0, 0.0};
-  if (L.kind == LK_KRON) {
-    // structured product already formed: rho = y - (A~ z)
-    if (active) {
-      const float* az = a.AZ + (int64_t)b * a.ldN;
+  const int32_t* nzi = a.nz_idx + (int64_t)b * a.K;
+  const VT* nzv = a.nz_val + (int64_t)b * a.K;
+  const int N = (int)a.dd.N, ldN = (int)a.ldN;
+  const int ngroups = (ldN + RES_THREADS * 4 - 1) / (RES_THREADS * 4);
+  // FP64 data arithmetic (FP64 level, or FP32 data with FP64 accumulation) or FP64 iterates on
+  // a float level: FP64 sums of the residual
+  const bool fp64a = level_fp64_arith(L.kind);
+  const bool dsum = fp64a || sizeof(VT) == 8;
+  DF rrf, yrf;
+  rrf.init();
+  yrf.init();
+  double rrd = 0.0, yrd = 0.0;
+  for (int grp = 0; grp < ngroups; ++grp) {
+    const int r0 = grp * RES_THREADS * 4 + threadIdx.x * 4;
+    const bool active = r0 < N;
+    if (fp64a) {
+      double out[4] = {0.0, 0.0, 0.0, 0.0};
+      if (L.kind == LK_KRON) {
+        if (active) {
+          const float* az = a.AZ + (int64_t)b * a.ldN;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) out[v] = (double)y[r0 + v] - (double)az[r0 + v];
-    }
-  } else if (level_fp64_arith(L.kind)) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const int nnz = s.n_nz;
-    for (int base = 0; base < nnz; base += RES_THREADS) {
-      __syncthreads();
-      if (base + threadIdx.x < nnz) {
-        s_idx[threadIdx.x] = a.nz_idx[(int64_t)b * a.K + base + threadIdx.x];
-        s_val[threadIdx.x] = (double)a.nz_val[(int64_t)b * a.K + base + threadIdx.x];
-      }
-      __syncthreads();
-      const int cnt = min(RES_THREADS, nnz - base);
-      if (active)
-        for (int q = 0; q < cnt; ++q) {
-          D4 av = load4_d(L, s_idx[q], r0);
-          double w = s_val[q];
-          acc[0] = fma(w, av.x, acc[0]);
-          acc[1] = fma(w, av.y, acc[1]);
-          acc[2] = fma(w, av.z, acc[2]);
-          acc[3] = fma(w, av.w, acc[3]);
+          for (int v = 0; v < 4; ++v) out[v] = (double)y[r0 + v] - (double)az[r0 + v];
         }
-    }
-    if (active)
+      } else {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int base = 0; base < nnz; base += RES_THREADS) {
+          __syncthreads();
+          if (base + threadIdx.x < nnz) {
+            s_idx[threadIdx.x] = nzi[base + threadIdx.x];
+            s_wd[threadIdx.x] = (double)nzv[base + threadIdx.x];
+          }
+          __syncthreads();
+          const int cnt = min(RES_THREADS, nnz - base);
+          if (active)
+            for (int q = 0; q < cnt; ++q) {
+              const D4 av = load4_d(L, s_idx[q], r0);
+              const double w = s_wd[q];
+              acc[0] = fma(w, av.x, acc[0]);
+              acc[1] = fma(w, av.y, acc[1]);
+              acc[2] = fma(w, av.z, acc[2]);
+              acc[3] = fma(w, av.w, acc[3]);
+            }
+        }
+        if (active)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) out[v] = (double)y[r0 + v] - acc[v];
-  } else {
+          for (int v = 0; v < 4; ++v) out[v] = (double)y[r0 + v] - acc[v];
+      }
+      if (r0 < ldN) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          if (r0 + v < N) {
+            const VT r = (VT)out[v];
+            rho[r0 + v] = r;
+            rrd = fma((double)r, (double)r, rrd);
+            yrd = fma((double)y[r0 + v], (double)r, yrd);
+          } else {
+            rho[r0 + v] = (VT)0;
+          }
+        }
+      }
+      continue;
+    }
+    // FP32 iterates on a float level: double-float accumulation of the products (Dot2 on the
+    // exact FP32 level, exact pairs on BF16 / FP8), FP32 result y - (s + c)
     DF acc[4];
-    float p[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v].init();
-    const int nnz = s.n_nz;
-    int parity = 0;
-    for (int base = 0; base < nnz; base += RES_THREADS) {
-      __syncthreads();
-      if (base + threadIdx.x < nnz) {
-        int32_t j = a.nz_idx[(int64_t)b * a.K + base + threadIdx.x];
-        float w = (float)a.nz_val[(int64_t)b * a.K + base + threadIdx.x];
-        if (L.kind == LK_FP8) w = __fmul_rn(w, L.scale[j]);
-        s_idx[threadIdx.x] = j;
-        s_val[threadIdx.x] = (double)w;
+    if (L.kind == LK_KRON) {
+      if (active) {
+        const float* az = a.AZ + (int64_t)b * a.ldN;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v].s = az[r0 + v];
       }
-      __syncthreads();
-      const int cnt = min(RES_THREADS, nnz - base);
-      if (active && L.kind == LK_F32) {
-        for (int q = 0; q < cnt; ++q) {
-          float4 av = load4_f(L, s_idx[q], r0);
-          float w = (float)s_val[q];
-          dot2_add(acc[0], w, av.x);
-          dot2_add(acc[1], w, av.y);
-          dot2_add(acc[2], w, av.z);
-          dot2_add(acc[3], w, av.w);
+    } else {
+      float p[4] = {0.f, 0.f, 0.f, 0.f};
+      int parity = 0;
+      for (int base = 0; base < nnz; base += RES_THREADS) {
+        __syncthreads();
+        if (base + threadIdx.x < nnz) {
+          const int32_t j = nzi[base + threadIdx.x];
+          float w = (float)nzv[base + threadIdx.x];
+          if (L.kind == LK_FP8) w = __fmul_rn(w, L.scale[j]);
+          s_idx[threadIdx.x] = j;
+          s_wf[threadIdx.x] = w;
         }
-      } else if (active)
-        for (int q = 0; q < cnt; ++q) {
-          float4 av = load4_f(L, s_idx[q], r0);
-          float w = (float)s_val[q];
-          if (parity == 0) {
-            p[0] = __fmul_rn(w, av.x);
-            p[1] = __fmul_rn(w, av.y);
-            p[2] = __fmul_rn(w, av.z);
-            p[3] = __fmul_rn(w, av.w);
-          } else {
-            acc[0].add(__fmaf_rn(w, av.x, p[0]));
-            acc[1].add(__fmaf_rn(w, av.y, p[1]));
-            acc[2].add(__fmaf_rn(w, av.z, p[2]));
-            acc[3].add(__fmaf_rn(w, av.w, p[3]));
+        __syncthreads();
+        const int cnt = min(RES_THREADS, nnz - base);
+        if (active && L.kind == LK_F32) {
+          for (int q = 0; q < cnt; ++q) {
+            const float4 av = load4_f(L, s_idx[q], r0);
+            const float w = s_wf[q];
+            dot2_add(acc[0], w, av.x);
+            dot2_add(acc[1], w, av.y);
+            dot2_add(acc[2], w, av.z);
+            dot2_add(acc[3], w, av.w);
           }
-          parity ^= 1;
+        } else if (active) {
+          for (int q = 0; q < cnt; ++q) {
+            const float4 av = load4_f(L, s_idx[q], r0);
+            const float w = s_wf[q];
+            if (parity == 0) {
+              p[0] = __fmul_rn(w, av.x);
+              p[1] = __fmul_rn(w, av.y);
+              p[2] = __fmul_rn(w, av.z);
+              p[3] = __fmul_rn(w, av.w);
+            } else {
+              acc[0].add(__fmaf_rn(w, av.x, p[0]));
+              acc[1].add(__fmaf_rn(w, av.y, p[1]));
+              acc[2].add(__fmaf_rn(w, av.z, p[2]));
+              acc[3].add(__fmaf_rn(w, av.w, p[3]));
+            }
+            parity ^= 1;
+          }
         }
-    }
-    if (active) {
-      if (parity) {
+      }
+      if (active && parity) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[v].add(p[v]);
       }
-#pragma unroll
-      for (int v = 0; v < 4; ++v) out[v] = (double)y[r0 + v] - acc[v].value();
     }
-  }
-  double rr = 0.0, yr = 0.0;
-  if (writer) {
+    if (sizeof(VT) == 8 && r0 < ldN) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      if (r0 + v < a.dd.N) {
-        VT r = (VT)out[v];
-        rho[r0 + v] = r;
-        rr = fma((double)r, (double)r, rr);
-        yr = fma((double)y[r0 + v], (double)r, yr);
-      } else {
-        rho[r0 + v] = (VT)0;
+      for (int v = 0; v < 4; ++v) {
+        if (r0 + v < N) {
+          const double out = (double)y[r0 + v] - acc[v].value();
+          const VT r = (VT)out;
+          rho[r0 + v] = r;
+          rrd = fma((double)r, (double)r, rrd);
+          yrd = fma((double)y[r0 + v], (double)r, yrd);
+        } else {
+          rho[r0 + v] = (VT)0;
+        }
+      }
+    } else if (r0 < ldN) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        if (r0 + v < N) {
+          const float yv = (float)y[r0 + v];
+          // y - (s + c): TwoSum of y - s, then the small terms
+          float t, e;
+          two_sum(yv, -acc[v].s, t, e);
+          const float r = __fadd_rn(t, __fsub_rn(e, acc[v].c));
+          rho[r0 + v] = (VT)r;
+          dot2_add(rrf, r, r);
+          dot2_add(yrf, yv, r);
+        } else {
+          rho[r0 + v] = (VT)0;
+        }
       }
     }
   }
-  rr = warp_sum(rr);
-  yr = warp_sum(yr);
-  if ((threadIdx.x & 31) == 0) {
-    s_red[0][threadIdx.x >> 5] = rr;
-    s_red[1][threadIdx.x >> 5] = yr;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (dsum) {
+    rrd = warp_sum(rrd);
+    yrd = warp_sum(yrd);
+    if (lane == 0) {
+      s_red[0][wid] = rrd;
+      s_red[1][wid] = 0.0;
+      s_red[2][wid] = yrd;
+      s_red[3][wid] = 0.0;
+    }
+  } else {
+    rrf = df_warp_reduce(rrf);
+    yrf = df_warp_reduce(yrf);
+    if (lane == 0) {
+      s_red[0][wid] = rrf.s;
+      s_red[1][wid] = rrf.c;
+      s_red[2][wid] = yrf.s;
+      s_red[3][wid] = yrf.c;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t0 = 0.0, t1 = 0.0;
+    double rr = 0.0, yr = 0.0;
     for (int w = 0; w < RES_THREADS / 32; ++w) {
-      t0 += s_red[0][w];
-      t1 += s_red[1][w];
+      rr += s_red[0][w] + s_red[1][w];
+      yr += s_red[2][w] + s_red[3][w];
     }
-    double* pr = a.part_res + ((int64_t)b * a.nrb + blockIdx.x) * 2;
-    pr[0] = t0;
-    pr[1] = t1;
-    if (a.alg_bytes && blockIdx.x == 0 && L.kind != LK_KRON) {
+    sp->rr = rr;
+    sp->yr = yr;
+    sp->nrho_ru = __double2float_ru(sqrt(rr));
+    sp->thr_f = (float)(sp->lam * a.sp.inv_L);
+    sp->beta_f = (float)sp->beta;
+    if (a.alg_bytes && L.kind != LK_KRON) {
       // nonzero atoms of z (rows of A~), their values and indices, y read and rho written
       const double vs = (double)sizeof(VT);
-      atomicAdd(&a.alg_bytes[0], (double)s.n_nz * ((double)a.dd.N * level_elem_bytes(L.kind) + 4.0 + vs) +
-                                     2.0 * a.dd.N * vs);
+      atomicAdd(&a.alg_bytes[0], (double)nnz * ((double)N * level_elem_bytes(L.kind) + 4.0 + vs) + 2.0 * N * vs);
     }
   }
 }
@@ -516,7 +588,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
     if (MODE == CORR_INIT) {
       rr = s.yy;
     } else {
-      for (int q = 0; q < a.nrb; ++q) rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
+      rr = s.rr;
     }
     const double nrho = sqrt(rr);
     const double ug = fp64a && sizeof(VT) == 8 ? U64 : U32;
@@ -645,6 +717,132 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
 }
 
 // lambda_max bounds, lambda, early exit when lambda >= lambda_max (x* = 0, gap 0).
+// Signal of work item `item`: the last b in [lo, hi] with offsets[b] <= item.
+__device__ __forceinline__ int item_signal(const int* __restrict__ offsets, int lo, int hi, int item) {
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (offsets[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The correlation pass for FP32 iterates: g_j = a~_j^T rho^ over the preserved list, fused with
+// the FISTA update of those coefficients and with the two maxima of the pass,
+// max_j (|g_j| + eps_j ||rho^||) (upper bound, stable scaling) and max_j |g_j|.
+// Each block takes a contiguous range of (signal, chunk) items, so the signal's scalars are read
+// once per signal; each warp takes chunk / 8 consecutive positions of an item: lane l holds
+// position l (index, x, z and bound loaded up front), the warp forms the dot products two atoms
+// at a time, and the lanes then update their own coefficients in parallel.  The maxima go to
+// the signal's state with atomicMax on FP32 bit patterns (non-negative values), so no block
+// barrier is needed.  Every per-atom operation is FP32; the bounds use directed rounding.
+template <typename VT>
+__global__ void __launch_bounds__(CORR_THREADS, 4) k_corr_pass(PassArgs<VT> a) {
+  static_assert(sizeof(VT) == 4, "FP32 iterates only");
+  constexpr int NW = CORR_THREADS / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int B = a.sp.B;
+  const int total = a.offsets[B];
+  const int CH = a.sp.chunk;
+  const int PW = CH / NW;
+  const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int i0 = (int)blockIdx.x * per, i1 = min(total, i0 + per);
+  if (i0 >= i1) return;
+  const int ldN = (int)a.ldN;
+  const float ga_fac = 1.0000004f;   // >= 1 + 3 u32, rounded up
+  const float inv_Lf = (float)a.sp.inv_L;
+  const bool fista = a.sp.algo == LASSO_FISTA;
+  float bytes = 0.f;
+  int b = -1, b_first = 0, b_end = 0;
+  int lvl = 0, n_kept = 0;
+  bool from_full = false, tc = false;
+  float nrho_f = 0.f, thr_f = 0.f, beta_f = 0.f, dq_f = 0.f;
+  const int32_t* kp = nullptr;
+  VT *X = nullptr, *Z = nullptr, *G = nullptr;
+  const VT* rho = nullptr;
+  float m1 = 0.f, m2 = 0.f;
+  for (int item = i0; item < i1; ++item) {
+    if (item >= b_end) {
+      if (b >= 0) {
+        // flush the previous signal's maxima
+        m1 = warp_max_f(m1);
+        m2 = warp_max_f(m2);
+        if (lane == 0) {
+          atomicMax(&a.st[b].pm1, __float_as_uint(m1));
+          atomicMax(&a.st[b].pm2, __float_as_uint(m2));
+        }
+      }
+      b = item_signal(a.offsets, b + 1, B - 1, item);
+      b_first = a.offsets[b];
+      b_end = a.offsets[b + 1];
+      const SigState& s = a.st[b];
+      lvl = s.level;
+      n_kept = s.n_kept;
+      nrho_f = s.nrho_ru;
+      thr_f = s.thr_f;
+      beta_f = s.beta_f;
+      const LevelDev& L = a.dd.lv[lvl];
+      tc = L.tc != 0;
+      from_full = L.kind == LK_KRON || tc;
+      dq_f = tc ? __double2float_ru(s.dq * 1.001) : 0.f;
+      kp = kept_of(a, b, s.parity);
+      X = a.X + (int64_t)b * a.K;
+      Z = a.Z + (int64_t)b * a.K;
+      G = a.G + (int64_t)b * a.K;
+      rho = a.Rho + (int64_t)b * a.ldN;
+      m1 = 0.f;
+      m2 = 0.f;
+    }
+    if (a.alg_bytes && !from_full && item == b_first && wid == 0 && lane == 0) bytes += (float)a.dd.N * sizeof(VT);
+    const LevelDev& L = a.dd.lv[lvl];
+    const int q0 = (item - b_first) * CH + wid * PW;
+    const int cnt = min(PW, n_kept - q0);
+    if (cnt <= 0) continue;
+    const bool mine = lane < cnt;
+    const int pos = q0 + lane;
+    const int32_t j = mine ? kp[pos] : 0;
+    float xj = 0.f, zj = 0.f, er = 0.f, kq = 0.f, g = 0.f;
+    if (mine) {
+      xj = (float)X[j];
+      zj = (float)Z[j];
+      er = L.epsr32[j];
+      if (dq_f > 0.f) kq = L.kappa32[j];
+      if (from_full) g = a.Gfull[(int64_t)b * a.K + j];
+    }
+    if (!from_full) {
+      for (int q = 0; q < cnt; q += 2) {
+        const int j0 = __shfl_sync(0xffffffffu, j, q);
+        const int j1 = __shfl_sync(0xffffffffu, j, q + 1 < cnt ? q + 1 : q);
+        float g0, g1;
+        warp_atom_dot2_fast<VT>(L, j0, j1, ldN, rho, lane, g0, g1);
+        g = lane == q ? g0 : (lane == q + 1 ? g1 : g);
+      }
+      if (a.alg_bytes && lane == 0)
+        bytes += (float)cnt * ((float)a.dd.N * level_elem_bytes(L.kind) + 4.f + 5.f * sizeof(VT));
+    }
+    if (mine) {
+      const float ag = fabsf(g);
+      float ub = __fmaf_ru(er, nrho_f, __fmul_ru(ag, ga_fac));
+      if (dq_f > 0.f) ub = __fmaf_ru(kq, dq_f, ub);
+      m1 = fmaxf(m1, ub);
+      m2 = fmaxf(m2, ag);
+      const float v = __fmaf_rn(g, inv_Lf, zj);
+      const float xn = v > thr_f ? v - thr_f : (v < -thr_f ? v + thr_f : 0.f);
+      const float zn = fista ? __fmaf_rn(beta_f, xn - xj, xn) : xn;
+      X[j] = (VT)xn;
+      Z[j] = (VT)zn;
+      G[pos] = (VT)g;
+    }
+  }
+  m1 = warp_max_f(m1);
+  m2 = warp_max_f(m2);
+  if (lane == 0) {
+    atomicMax(&a.st[b].pm1, __float_as_uint(m1));
+    atomicMax(&a.st[b].pm2, __float_as_uint(m2));
+    if (a.alg_bytes && bytes > 0.f) atomicAdd(&a.alg_bytes[1], (double)bytes);
+  }
+}
+
 template <typename VT>
 __global__ void k_init_finish(PassArgs<VT> a, int lambda_relative) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -681,20 +879,27 @@ __global__ void k_init_finish(PassArgs<VT> a, int lambda_relative) {
 //   G' = P - D(theta'), G~ = P - D(theta~), delta = ||rho|| e + e^2/2 with
 //   e = sum eps_j |z_j| + (residual rounding), R' = sqrt(2 G' + 2 delta) / lam,
 //   gamma = G~ / G', stop when the level is exact and (G' + delta) / ||y||^2 <= tol.
-// Then every preserved atom is tested (stable GAP or Dynamic Safe sphere), K_t is counted,
-// Algorithm 2 picks the next level, and the preserved list, the nonzero list of z+ and their
-// sums are compacted in order.
+// Then, in one sweep of the preserved list, every atom is tested (stable GAP or Dynamic Safe
+// sphere), K_t is counted, and the preserved list and the nonzero list of z+ are compacted in
+// order; Algorithm 2 picks the next level and the sums of the nonzero list close the pass.
+// FP32 iterates keep the per-atom work in FP32: tests rounded upward (over-estimating only
+// keeps atoms), sum |z_j| compensated, sum eps_j |z_j| and sum kappa_j |z_j| rounded upward.
 template <typename VT>
-__global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
+__global__ void __launch_bounds__(SCREEN_THREADS, 3) k_screen(PassArgs<VT> a) {
+  constexpr bool F32 = sizeof(VT) == 4;
+  constexpr int NWS = SCREEN_THREADS / 32;
   const int b = blockIdx.x;
   SigState* sp = a.st + b;
-  if (sp->done) return;
   __shared__ double sc[16];
-  __shared__ int si[8];
-  __shared__ int s_warp[SCREEN_THREADS / 32];
-  __shared__ int s_warp2[SCREEN_THREADS / 32];
-  __shared__ double s_red[3][SCREEN_THREADS / 32];
-  __shared__ double s_wmax[SCREEN_THREADS / 32];
+  __shared__ int si[12];
+  constexpr int SU = 4;
+  __shared__ int s_cnt[2][SU][NWS];
+  __shared__ int s_warp3[NWS];
+  __shared__ double s_red[3][NWS];
+  __shared__ double s_wmax[NWS];
+  if (threadIdx.x == 0) si[11] = sp->done;
+  __syncthreads();
+  if (si[11]) return;
   const int I = a.dd.n_levels - 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // FP64 scalars of the pass for a given upper bound m1 of max_j (|a_j^T rho| + eps_j ||rho||)
@@ -725,14 +930,18 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
   if (threadIdx.x == 0) {
     SigState s = *sp;
     const LevelDev& L = a.dd.lv[s.level];
-    double rr = 0.0, yr = 0.0, m1 = 0.0, m2 = 0.0;
-    for (int q = 0; q < a.nrb; ++q) {
-      rr += a.part_res[((int64_t)b * a.nrb + q) * 2];
-      yr += a.part_res[((int64_t)b * a.nrb + q) * 2 + 1];
-    }
-    for (int c = 0; c < s.n_chunks; ++c) {
-      m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
-      m2 = fmax(m2, a.part_corr[((int64_t)b * a.nch + c) * 2 + 1]);
+    const double rr = s.rr, yr = s.yr;
+    double m1 = 0.0, m2 = 0.0;
+    if constexpr (F32) {
+      m1 = (double)__uint_as_float(s.pm1);
+      m2 = (double)__uint_as_float(s.pm2);
+      s.pm1 = 0u;
+      s.pm2 = 0u;
+    } else {
+      for (int c = 0; c < s.n_chunks; ++c) {
+        m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
+        m2 = fmax(m2, a.part_corr[((int64_t)b * a.nch + c) * 2 + 1]);
+      }
     }
     const double gcert = evaluate(s, L, rr, yr, m1, m2);
     s.iters += 1;
@@ -742,7 +951,7 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
     // margins already meets tol, the atoms that can attain the maximum are recomputed with
     // error-free products (below) to tighten the certificate.
     int refine = 0;
-    if (L.kind == LK_F32 && s.level == I && gcert > a.sp.tol && rr > 0.0 && m2 > 0.0) {
+    if (F32 && L.kind == LK_F32 && s.level == I && gcert > a.sp.tol && rr > 0.0 && m2 > 0.0) {
       SigState t = s;
       const double mest = m2 * (1.0 + 3.0 * U32);
       if (evaluate(t, L, rr, yr, mest, m2) <= a.sp.tol) refine = 1;
@@ -754,41 +963,60 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
     sc[12] = gcert;
     sc[13] = m1;
     si[1] = refine;
+    si[4] = s.n_kept;
+    si[5] = s.parity;
+    si[6] = s.level;
+    si[7] = s.n_nz;
     *sp = s;
   }
   __syncthreads();
-  if (si[1]) {
-    // candidates: atoms whose loose upper bound exceeds max_j |g^_j|; every other atom is below it
-    const SigState& s = *sp;
-    const LevelDev& L = a.dd.lv[s.level];
-    const double T = sc[11], nrho = sqrt(sc[8]);
-    const int32_t* kp = kept_of(a, b, s.parity);
-    const VT* G = a.G + (int64_t)b * a.K;
-    const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
-    double wm = 0.0;
-    for (int pos = wid; pos < s.n_kept; pos += SCREEN_THREADS / 32) {
-      const int64_t j = kp[pos];
-      const double ub = fabs((double)G[pos]) * (1.0 + 3.0 * U32) + L.gam_corr * L.kappa[j] * nrho;
-      if (ub > T) {
-        const double g = warp_atom_dot(L, j, (int)a.ldN, rho, nullptr, lane);
-        wm = fmax(wm, fabs(g) * (1.0 + 3.0 * U32) + L.gam_tight * L.kappa[j] * nrho);
+  const int n_kept = si[4], parity = si[5], level = si[6], n_nz = si[7];
+  const LevelDev& L = a.dd.lv[level];
+  const int32_t* kp = kept_of(a, b, parity);
+  const VT* G = a.G + (int64_t)b * a.K;
+  if constexpr (F32) {
+    if (si[1]) {
+      // candidates: atoms whose loose upper bound exceeds max_j |g^_j| (every other atom is
+      // below that maximum); the lanes test 32 positions at once, the warp recomputes each
+      // candidate with error-free products
+      const double T = sc[11], nrho = sqrt(sc[8]);
+      const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
+      const float T_f = __double2float_rd(T);
+      const float gn_f = __double2float_ru(L.gam_corr * nrho);
+      double wm = 0.0;
+      for (int base = wid * 32; base < n_kept; base += SCREEN_THREADS) {
+        const int pos = base + lane;
+        int32_t j = 0;
+        bool cand = false;
+        if (pos < n_kept) {
+          j = kp[pos];
+          const float ub = __fmaf_ru(L.kappa32[j], gn_f, __fmul_ru(fabsf((float)G[pos]), 1.0000004f));
+          cand = ub > T_f;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, cand);
+        while (m) {
+          const int l = __ffs(m) - 1;
+          m &= m - 1;
+          const int64_t jj = __shfl_sync(0xffffffffu, j, l);
+          const double g = warp_atom_dot(L, jj, (int)a.ldN, rho, nullptr, lane);
+          wm = fmax(wm, fabs(g) * (1.0 + 3.0 * U32) + L.gam_tight * L.kappa[jj] * nrho);
+        }
       }
+      if (lane == 0) s_wmax[wid] = wm;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double m1 = T;
+        for (int w = 0; w < NWS; ++w) m1 = fmax(m1, s_wmax[w]);
+        SigState s2 = *sp;
+        sc[13] = fmin(m1, sc[10]);
+        sc[12] = evaluate(s2, L, sc[8], sc[9], sc[13], sc[11]);
+        *sp = s2;
+      }
+      __syncthreads();
     }
-    if (lane == 0) s_wmax[wid] = wm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double m1 = T;
-      for (int w = 0; w < SCREEN_THREADS / 32; ++w) m1 = fmax(m1, s_wmax[w]);
-      SigState s2 = *sp;
-      sc[13] = fmin(m1, sc[10]);
-      sc[12] = evaluate(s2, L, sc[8], sc[9], sc[13], sc[11]);
-      *sp = s2;
-    }
-    __syncthreads();
   }
   if (threadIdx.x == 0) {
     SigState s = *sp;
-    const LevelDev& L = a.dd.lv[s.level];
     const double rr = sc[8], yr = sc[9], gcert = sc[12];
     const double lam = s.lam;
     const double nrho = sqrt(rr);
@@ -811,6 +1039,7 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
       s.c_kapz = s.sum_kapz;
       s.c_nnz = s.n_nz;
       s.c_m1 = sc[13];
+      s.c_nrho_ru = __double2float_ru(nrho);
       si[2] = 1;
     } else if (s.iters >= a.sp.max_iter) {
       s.status = LASSO_ERR_MAXITER;
@@ -826,6 +1055,7 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
       s.c_kapz = s.sum_kapz;
       s.c_nnz = s.n_nz;
       s.c_m1 = sc[13];
+      s.c_nrho_ru = __double2float_ru(nrho);
     }
     // Dynamic Safe radius ||theta' - y/lam|| (Table I)
     const double sp_ = s.sp;
@@ -835,37 +1065,34 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
     sc[1] = fabs(sp_) * nrho;
     sc[2] = a.sp.rule == LASSO_RULE_GAP ? s.Rp : sqrt(fmax(d2, 0.0));
     sc[5] = 1.0 - a.sp.tau;
-    sc[6] = 1.0 + 3.0 * (level_fp64_arith(L.kind) && sizeof(VT) == 8 ? U64 : U32);
+    sc[6] = 1.0 + 3.0 * (level_fp64_arith(a.dd.lv[s.level].kind) && sizeof(VT) == 8 ? U64 : U32);
     sc[7] = 1.0 / lam;
+    sc[14] = s.dq;
     si[0] = action;
     si[1] = screen ? 1 : 0;
     *sp = s;
   }
   __syncthreads();
   const int action = si[0];
-  SigState s = *sp;
-  const int32_t* kp = kept_of(a, b, s.parity);
   VT* X = a.X + (int64_t)b * a.K;
   VT* Z = a.Z + (int64_t)b * a.K;
-  const VT* G = a.G + (int64_t)b * a.K;
   if (action) {
     // return the certified point z_t (its nonzero list) and stop
     VT* xo = a.Xout + (int64_t)b * a.K;
-    for (int q = threadIdx.x; q < s.n_nz; q += SCREEN_THREADS)
+    for (int q = threadIdx.x; q < n_nz; q += SCREEN_THREADS)
       xo[a.nz_idx[(int64_t)b * a.K + q]] = a.nz_val[(int64_t)b * a.K + q];
     if (threadIdx.x == 0) sp->done = 1;
     return;
   }
   if (si[2]) {
-    for (int q = threadIdx.x; q < s.n_nz; q += SCREEN_THREADS) {
+    for (int q = threadIdx.x; q < n_nz; q += SCREEN_THREADS) {
       a.cand_idx[(int64_t)b * a.K + q] = a.nz_idx[(int64_t)b * a.K + q];
       a.cand_val[(int64_t)b * a.K + q] = a.nz_val[(int64_t)b * a.K + q];
     }
   }
-  const LevelDev& L = a.dd.lv[s.level];
   const bool screen = si[1];
   const double abs_sp = sc[0], c_eps = sc[1], Rs = sc[2], abs_st = sc[3], Rt = sc[4], thr = sc[5], gfac = sc[6],
-               inv_lam = sc[7];
+               inv_lam = sc[7], dq = sc[14];
   const bool gap_rule = a.sp.rule == LASSO_RULE_GAP;
   const double* anorm = a.dd.anorm;
   const float* anorm32 = a.dd.anorm32;
@@ -876,121 +1103,180 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
   const float c_eps_f = __double2float_ru(c_eps), Rs_f = __double2float_ru(Rs);
   const float inv_lam_f = __double2float_ru(inv_lam), thr_f = __double2float_rd(thr);
   const float abs_st_f = (float)abs_st, Rt_f = (float)Rt;
-  const float c_dq_f = L.tc ? __double2float_ru(abs_sp * s.dq * 1.001) : 0.f;
-  auto keep_of = [&](int pos, int64_t j, double& mu_out) -> bool {
+  const float c_dq_f = L.tc ? __double2float_ru(abs_sp * dq * 1.001) : 0.f;
+  auto keep_of = [&](int64_t j, VT g) -> bool {
     if (!screen) return true;
-    if constexpr (sizeof(VT) == 4) {
+    if constexpr (F32) {
       float mu;
       if (gap_rule) {
-        mu = __fadd_ru(__fmaf_ru(L.epsr32[j], c_eps_f, __fmul_ru(__fmul_ru(abs_sp_f, fabsf((float)G[pos])), gfac_f)),
+        mu = __fadd_ru(__fmaf_ru(L.epsr32[j], c_eps_f, __fmul_ru(__fmul_ru(abs_sp_f, fabsf((float)g)), gfac_f)),
                        __fmul_ru(Rs_f, anorm32[j]));
         if (c_dq_f > 0.f) mu = __fmaf_ru(L.kappa32[j], c_dq_f, mu);
-      }
-      else
+      } else {
         mu = __fadd_ru(__fmul_ru(c0[j], inv_lam_f), __fmul_ru(Rs_f, anorm32[j]));
-      mu_out = mu;
+      }
       return mu >= thr_f;
     } else {
       double mu;
       if (gap_rule)
-        mu = abs_sp * fabs((double)G[pos]) * gfac + (L.eps[j] + L.gam_corr * L.kappa[j]) * c_eps + Rs * anorm[j] +
-             (L.tc ? L.kappa[j] * abs_sp * s.dq * 1.001 : 0.0);
+        mu = abs_sp * fabs((double)g) * gfac + (L.eps[j] + L.gam_corr * L.kappa[j]) * c_eps + Rs * anorm[j] +
+             (L.tc ? L.kappa[j] * abs_sp * dq * 1.001 : 0.0);
       else mu = (double)c0[j] * inv_lam + Rs * anorm[j];
-      mu_out = mu * (1.0 + 4.0 * U64);
-      return mu >= thr;
+      return mu * (1.0 + 4.0 * U64) >= thr;
     }
   };
-  // ---- phase 1: look-ahead estimate K_t (conventional test on A~, eq:DefCardinalEstimated)
-  int kt = 0;
-  for (int pos = threadIdx.x; pos < s.n_kept; pos += SCREEN_THREADS) {
-    const int64_t j = kp[pos];
-    if (__fmaf_rn(abs_st_f, fabsf((float)G[pos]), Rt_f * L.atnorm[j]) >= 1.f) ++kt;
+  // ---- one sweep: K_t (conventional test on A~, eq:DefCardinalEstimated), the stable test,
+  // and ordered compaction of the preserved list and of the nonzeros of z+
+  int32_t* kn = kept_of(a, b, parity ^ 1);
+  int32_t* nzi = a.nz_idx + (int64_t)b * a.K;
+  VT* nzv = a.nz_val + (int64_t)b * a.K;
+  int base_k = 0, base_z = 0, kt = 0;
+  DF l1f;
+  l1f.init();
+  float sef = 0.f, skf = 0.f;
+  double l1 = 0.0, se = 0.0, sk = 0.0;
+  // SU positions per thread per step (loads of all of them in flight together)
+  for (int t0 = 0; t0 < n_kept; t0 += SU * SCREEN_THREADS) {
+    int32_t jv[SU];
+    VT gv[SU], zv[SU];
+    bool keep[SU], nz[SU];
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+      const int pos = t0 + u * SCREEN_THREADS + threadIdx.x;
+      jv[u] = pos < n_kept ? kp[pos] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+      const int pos = t0 + u * SCREEN_THREADS + threadIdx.x;
+      gv[u] = jv[u] >= 0 ? G[pos] : (VT)0;
+      zv[u] = jv[u] >= 0 ? Z[jv[u]] : (VT)0;
+    }
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+      keep[u] = false;
+      nz[u] = false;
+      if (jv[u] >= 0) {
+        const int64_t j = jv[u];
+        if (__fmaf_rn(abs_st_f, fabsf((float)gv[u]), Rt_f * L.atnorm[j]) >= 1.f) ++kt;
+        keep[u] = keep_of(j, gv[u]);
+        if (!keep[u]) {
+          X[j] = (VT)0;
+          Z[j] = (VT)0;
+          a.mask[(int64_t)b * a.K + j] = 0;
+        } else {
+          nz[u] = zv[u] != (VT)0;
+        }
+      }
+    }
+    unsigned bk[SU], bz[SU];
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+      bk[u] = __ballot_sync(0xffffffffu, keep[u]);
+      bz[u] = __ballot_sync(0xffffffffu, nz[u]);
+      if (lane == 0) {
+        s_cnt[0][u][wid] = __popc(bk[u]);
+        s_cnt[1][u][wid] = __popc(bz[u]);
+      }
+    }
+    __syncthreads();
+    // ordered offsets: position order is (u, warp, lane)
+    int off_k[SU], off_z[SU];
+    int run_k = base_k, run_z = base_z;
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+      for (int w = 0; w < NWS; ++w) {
+        if (w == wid) {
+          off_k[u] = run_k;
+          off_z[u] = run_z;
+        }
+        run_k += s_cnt[0][u][w];
+        run_z += s_cnt[1][u][w];
+      }
+    }
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+      if (keep[u]) kn[off_k[u] + __popc(bk[u] & below)] = jv[u];
+      if (nz[u]) {
+        const int64_t j = jv[u];
+        const int q = off_z[u] + __popc(bz[u] & below);
+        nzi[q] = jv[u];
+        nzv[q] = zv[u];
+        if constexpr (F32) {
+          const float az = fabsf((float)zv[u]);
+          l1f.add(az);
+          sef = __fmaf_ru(L.eps32[j], az, sef);
+          skf = __fmaf_ru(L.kappa32[j], az, skf);
+        } else {
+          const double az = fabs((double)zv[u]);
+          l1 += az;
+          se = fma(L.eps[j], az, se);
+          sk = fma(L.kappa[j], az, sk);
+        }
+      }
+    }
+    base_k = run_k;
+    base_z = run_z;
+    __syncthreads();
   }
   kt = warp_sum_i(kt);
-  if (lane == 0) s_warp[wid] = kt;
+  if (lane == 0) s_warp3[wid] = kt;
   __syncthreads();
   if (threadIdx.x == 0) {
     int t = 0;
-    for (int w = 0; w < SCREEN_THREADS / 32; ++w) t += s_warp[w];
+    for (int w = 0; w < NWS; ++w) t += s_warp3[w];
     // Algorithm 2
-    int nl = s.level;
-    if (s.level < I) {
+    int nl = level;
+    if (level < I) {
       if (t <= L.rc * (double)a.K) nl = I;
-      else if (s.gamma <= a.sp.Gamma) nl = s.level + 1;
+      else if (sp->gamma <= a.sp.Gamma) nl = level + 1;
     }
-    si[2] = nl;
-    si[3] = t;
+    si[8] = nl;
+    si[9] = t;
   }
   __syncthreads();
-  const int new_level = si[2];
-  const LevelDev& Ln = a.dd.lv[new_level];
-  // ---- phase 2: ordered compaction of the preserved list and of the nonzeros of z+
-  int32_t* kn = kept_of(a, b, s.parity ^ 1);
-  int32_t* nzi = a.nz_idx + (int64_t)b * a.K;
-  VT* nzv = a.nz_val + (int64_t)b * a.K;
-  int base_k = 0, base_z = 0;
-  double l1 = 0.0, se = 0.0, sk = 0.0;
-  for (int t0 = 0; t0 < s.n_kept; t0 += SCREEN_THREADS) {
-    const int pos = t0 + threadIdx.x;
-    bool keep = false, nz = false;
-    int64_t j = 0;
-    double zv = 0.0;
-    if (pos < s.n_kept) {
-      j = kp[pos];
-      double mu = 0.0;
-      keep = keep_of(pos, j, mu);
-      if (!keep) {
-        X[j] = (VT)0;
-        Z[j] = (VT)0;
-        a.mask[(int64_t)b * a.K + j] = 0;
+  const int new_level = si[8];
+  if (new_level != level) {
+    // the error sums of the nonzero list belong to the level of the next pass
+    const LevelDev& Ln = a.dd.lv[new_level];
+    sef = skf = 0.f;
+    se = sk = 0.0;
+    for (int q = threadIdx.x; q < base_z; q += SCREEN_THREADS) {
+      const int64_t j = nzi[q];
+      if constexpr (F32) {
+        const float az = fabsf((float)nzv[q]);
+        sef = __fmaf_ru(Ln.eps32[j], az, sef);
+        skf = __fmaf_ru(Ln.kappa32[j], az, skf);
       } else {
-        zv = (double)Z[j];
-        nz = zv != 0.0;
+        const double az = fabs((double)nzv[q]);
+        se = fma(Ln.eps[j], az, se);
+        sk = fma(Ln.kappa[j], az, sk);
       }
     }
-    const unsigned bk = __ballot_sync(0xffffffffu, keep);
-    const unsigned bz = __ballot_sync(0xffffffffu, nz);
-    if (lane == 0) {
-      s_warp[wid] = __popc(bk);
-      s_warp2[wid] = __popc(bz);
-    }
-    __syncthreads();
-    int off_k = base_k, off_z = base_z, tot_k = 0, tot_z = 0;
-    for (int w = 0; w < SCREEN_THREADS / 32; ++w) {
-      if (w < wid) {
-        off_k += s_warp[w];
-        off_z += s_warp2[w];
-      }
-      tot_k += s_warp[w];
-      tot_z += s_warp2[w];
-    }
-    const unsigned below = (1u << lane) - 1u;
-    if (keep) kn[off_k + __popc(bk & below)] = (int32_t)j;
-    if (nz) {
-      const int q = off_z + __popc(bz & below);
-      nzi[q] = (int32_t)j;
-      nzv[q] = (VT)zv;
-      const double az = fabs(zv);
-      l1 += az;
-      se = fma(Ln.eps[j], az, se);
-      sk = fma(Ln.kappa[j], az, sk);
-    }
-    base_k += tot_k;
-    base_z += tot_z;
-    __syncthreads();
   }
-  l1 = warp_sum(l1);
-  se = warp_sum(se);
-  sk = warp_sum(sk);
-  if (lane == 0) {
-    s_red[0][wid] = l1;
-    s_red[1][wid] = se;
-    s_red[2][wid] = sk;
+  if constexpr (F32) {
+    l1f = df_warp_reduce(l1f);
+    sef = warp_sum_ru(sef);
+    skf = warp_sum_ru(skf);
+    if (lane == 0) {
+      s_red[0][wid] = (double)l1f.s + (double)l1f.c;
+      s_red[1][wid] = (double)sef;
+      s_red[2][wid] = (double)skf;
+    }
+  } else {
+    l1 = warp_sum(l1);
+    se = warp_sum(se);
+    sk = warp_sum(sk);
+    if (lane == 0) {
+      s_red[0][wid] = l1;
+      s_red[1][wid] = se;
+      s_red[2][wid] = sk;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double t1 = 0.0, t2 = 0.0, t3 = 0.0;
-    for (int w = 0; w < SCREEN_THREADS / 32; ++w) {
+    for (int w = 0; w < NWS; ++w) {
       t1 += s_red[0][w];
       t2 += s_red[1][w];
       t3 += s_red[2][w];
@@ -1001,12 +1287,13 @@ __global__ void __launch_bounds__(SCREEN_THREADS) k_screen(PassArgs<VT> a) {
     o.sum_kapz = t3;
     o.n_kept = base_k;
     o.n_nz = base_z;
-    o.Kt = si[3];
+    o.Kt = si[9];
     o.level = new_level;
-    o.parity = s.parity ^ 1;
+    o.parity = parity ^ 1;
     o.n_chunks = (base_k + a.sp.chunk - 1) / a.sp.chunk;
     // FISTA: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, momentum (t_k - 1) / t_{k+1} for the next update
-    const double t1n = 0.5 * (1.0 + sqrt(1.0 + 4.0 * s.t * s.t));
+    const double tk = o.t;
+    const double t1n = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
     const double t2n = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t1n * t1n));
     o.t = t1n;
     o.beta = (t1n - 1.0) / t2n;
@@ -1077,7 +1364,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_full_check(PassArgs<VT> a) {
     const SigState& s = a.st[b];
     const VT* rho = a.Rho + (int64_t)b * a.ldN;
     const uint8_t* mk = a.mask + (int64_t)b * a.K;
-    const float nrho_f = __double2float_ru(sqrt(s.c_rr));
+    const float nrho_f = s.c_nrho_ru;
     const int64_t j0 = (int64_t)chunk * CH, j1 = min((int64_t)a.K, j0 + CH);
     float m = 0.f;
     for (int64_t j = j0 + wid; j < j1; j += CORR_THREADS / 32) {
@@ -1467,7 +1754,7 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
     k_kron_gemm<VT, KS_Y><<<dim3(tiles(N2), tiles(N1), B), 256, 0, st>>>(pa);
   }
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
-  k_residual<VT><<<dim3(pa.nrb, B), RES_THREADS, 0, st>>>(pa);
+  k_residual<VT><<<B, RES_THREADS, 0, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
   if (has_kron) {
     const int Rmax = [&] {
@@ -1491,7 +1778,8 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   }
   if (ev) cudaEventRecordWithFlags(ev[8], st, cudaEventRecordExternal);
   if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
-  k_corr<VT, CORR_PASS><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
+  if constexpr (sizeof(VT) == 4) k_corr_pass<VT><<<corr_grid, CORR_THREADS, 0, st>>>(pa);
+  else k_corr<VT, CORR_PASS><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
   k_screen<VT><<<B, SCREEN_THREADS, 0, st>>>(pa);
   if (pa.sp.full_gap) {
@@ -1563,6 +1851,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   pa.sp.Gamma = o.Gamma;
   pa.sp.tau = o.tau;
   pa.sp.L = d->L;
+  pa.sp.inv_L = 1.0 / d->L;
   pa.sp.algo = o.algo;
   pa.sp.rule = o.rule;
   pa.sp.screen_every = std::max(1, o.screen_every);
@@ -1867,6 +2156,7 @@ static int run_lambda_max(lasso_dict* d, Workspace* w, const float* Y, int64_t B
   if (rc) return rc;
   pa.sp.B = (int)B;
   pa.sp.L = 1.0;
+  pa.sp.inv_L = 1.0;
   pa.sp.chunk = CORR_CHUNK;
   fill_pass_args(pa, w, d);
   if (trace_steps()) fprintf(stderr, "[lasso trace] lmax: arguments ready\n");
