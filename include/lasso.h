@@ -130,6 +130,14 @@ typedef struct {
                                 rejected atoms' correlations are evaluated when the preserved-set
                                 gap meets tol); 0: stop on the preserved-set gap, which bounds
                                 P(x) - P* only                                                  */
+    int tc_exact;            /* 1: with tensor_cores, the exact FP32 level's bulk correlation runs
+                                on the tensor cores in split form a = a1 + a2 (+ bounded rest),
+                                rho = r1 + r2 (+ bounded rest), three BF16 products in one FP32
+                                accumulator; its error bound enters the stable test like an
+                                approximation error, and the stopping certificate recomputes
+                                the deciding atoms from the FP32 data.  Default 0: the tensor
+                                cores' FP32 accumulation is too coarse for the last decades of
+                                the gap (FISTA needs more passes, some signals stall near 1e-6) */
 } lasso_opts;
 
 /* Fill *opts with the defaults above. */
@@ -201,13 +209,16 @@ int lasso_lambda_max_noalloc(const lasso_dict* dict, const float* d_Y, int64_t B
 int lasso_backward(lasso_dict* dict, const float* d_Y, const float* d_X, const float* d_G,
                    int64_t B, float* d_dY, float* d_dA, void* stream);
 
-/* Check of the tensor-core GEMM behind the batched BF16 / FP8 levels: B x K correlations of
- * random operands (N terms each; signed values, and all-positive values for the worst
- * accumulation) through tcgen05, compared with an FP64 evaluation of the same products.
- * max_rel_err: largest |error| / sum_i |a_i r_i|; max_err_over_bound: largest |error| over the
- * accumulation bound the stable test assumes (gamma_{N + N/k}(u_tc) sum_i |a_i r_i|, with
- * u_tc = 2^-22 for BF16 and 2^-19 for E4M3).  fp8: 1 = E4M3, 0 = BF16. */
-int lasso_tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel_err, double* max_err_over_bound);
+/* Check of the tensor-core GEMM behind the batched BF16 / FP8 levels and the split exact level:
+ * B x K correlations of random operands (N terms each; signed values, and all-positive values
+ * for the worst accumulation) through tcgen05, compared with an FP64 evaluation of the same
+ * products.  max_rel_err: largest |error| / sum_i |a_i r_i|; max_err_over_bound: largest |error|
+ * over the accumulation bound the stable test assumes (gamma_{n}(u_tc) sum_i |a_i r_i| with
+ * n = N + N/k products and k-steps, times 3 in split mode; u_tc = 2^-22 for BF16 and 2^-19
+ * for E4M3).  mode: 0 = BF16, 1 = E4M3, 2 = split BF16 (a1 r1 + a1 r2 + a2 r1 in one
+ * accumulator).  The paper has no counterpart: it checks an assumption of this build's
+ * rounding model (products treated as exact there). */
+int lasso_tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel_err, double* max_err_over_bound);
 
 const char* lasso_strerror(int status);
 

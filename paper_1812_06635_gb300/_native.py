@@ -28,6 +28,7 @@ class LassoOpts(C.Structure):
         ("time_limit_s", C.c_double),
         ("profile", C.c_int),
         ("full_gap", C.c_int),
+        ("tc_exact", C.c_int),
     ]
 
 

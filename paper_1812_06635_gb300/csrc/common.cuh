@@ -43,6 +43,13 @@ struct LevelDev {
   const float* epsr32;      // eps_j + gam_corr kappa_j rounded up to FP32 (bulk bound in FP32 code)
   const float* kappa32;     // kappa_j rounded up to FP32
   const float* eps32;       // eps_j rounded up to FP32
+  const float* epsr32_simt; // eps_j + (FP32 SIMT product bound) kappa_j: fast checks outside the bulk pass
+  // Split tensor-core form of the exact FP32 level: a = a1 + a2 + e3 (a1, a2 BF16), correlated as
+  // a1^T r1 + a1^T r2 + a2^T r1 with rho = r1 + r2 + r3; c2 >= max_j ||a2_j|| / kappa_j bounds the
+  // dropped a2^T r2 through the per-signal term (k_quant_rho folds c2 ||r2|| into dq).
+  int split;
+  double c2;
+  void* rq2;                // split: second BF16 operand of the residuals
   int tc;                   // 1: batched correlation on the tensor cores (BF16 / FP8 levels)
   void* rq;                 // tensor-core levels: quantised residuals (B x ld, BF16 or E4M3)
   float* rsig;              // tensor-core levels: per-signal scale of the quantised residual

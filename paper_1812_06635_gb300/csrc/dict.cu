@@ -267,6 +267,75 @@ __global__ void k_round_up_f32(const double* __restrict__ eps, const double* __r
     out[j] = __double2float_ru(kappa ? eps[j] + gam * kappa[j] : eps[j]);
 }
 
+static int grid_for(int64_t n, int threads = 256) {
+  int64_t g = (n + threads - 1) / threads;
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 1 << 20);
+}
+
+__global__ void k_round_up3_f32(const double* __restrict__ eps, const double* __restrict__ kappa, double gam,
+                                const double* __restrict__ extra, int64_t K, float* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = __double2float_ru((eps[j] + gam * kappa[j] + extra[j]) * (1.0 + 4.0 * U64));
+}
+
+// BF16 split of the FP32 exact atoms, one warp per atom: a1 = bf16(a), a2 = bf16(a - a1) (both
+// differences are exact in FP32), the remainder norm ||a - a1 - a2|| and ||a2|| / kappa_j.
+__global__ void k_split_bf16(const float* __restrict__ A, int64_t K, int64_t ld, const double* __restrict__ kappa,
+                             __nv_bfloat16* __restrict__ s1, __nv_bfloat16* __restrict__ s2, double* __restrict__ e3,
+                             double* __restrict__ ratio2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (j >= K) return;
+  double se = 0.0, s2n = 0.0;
+  for (int64_t n = lane; n < ld; n += 32) {
+    const float a = A[j * ld + n];
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(a);
+    const float r1 = __fsub_rn(a, __bfloat162float(h1));
+    const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+    const float r2 = __fsub_rn(r1, __bfloat162float(h2));
+    s1[j * ld + n] = h1;
+    s2[j * ld + n] = h2;
+    se = fma((double)r2, (double)r2, se);
+    const double v2 = (double)__bfloat162float(h2);
+    s2n = fma(v2, v2, s2n);
+  }
+  se = warp_sum(se);
+  s2n = warp_sum(s2n);
+  if (lane == 0) {
+    e3[j] = sqrt(se) * (1.0 + 1e-12);
+    ratio2[j] = kappa[j] > 0.0 ? sqrt(s2n) * (1.0 + 1e-12) / kappa[j] : 0.0;
+  }
+}
+
+int ensure_split(lasso_dict* d) {
+  HostLevel& h = d->exact;
+  if (h.split1) return LASSO_OK;
+  if (h.kind != LK_F32 || !h.data || !h.kappa) return LASSO_ERR_INVALID_ARG;
+  const size_t elems = (size_t)d->K * d->ldN;
+  double* ratio = nullptr;
+  if (cudaMalloc(&h.split1, elems * 2) != cudaSuccess || cudaMalloc(&h.split2, elems * 2) != cudaSuccess ||
+      cudaMalloc(&h.e3, d->K * sizeof(double)) != cudaSuccess || cudaMalloc(&ratio, d->K * sizeof(double)) != cudaSuccess) {
+    cudaFree(h.split1);
+    cudaFree(h.split2);
+    cudaFree(h.e3);
+    cudaFree(ratio);
+    h.split1 = h.split2 = nullptr;
+    h.e3 = nullptr;
+    set_last_error("no device memory for the BF16 split of the dictionary", __FILE__, __LINE__);
+    return LASSO_ERR_NOMEM;
+  }
+  k_split_bf16<<<grid_for(d->K * 32), 256>>>((const float*)h.data, d->K, d->ldN, h.kappa,
+                                                (__nv_bfloat16*)h.split1, (__nv_bfloat16*)h.split2, h.e3, ratio);
+  LASSO_CUDA_TRY(cudaGetLastError());
+  std::vector<double> r(d->K);
+  LASSO_CUDA_TRY(cudaMemcpy(r.data(), ratio, d->K * sizeof(double), cudaMemcpyDeviceToHost));
+  cudaFree(ratio);
+  double c2 = 0.0;
+  for (double v : r) c2 = std::max(c2, v);
+  h.c2 = c2 * (1.0 + 1e-9);
+  return LASSO_OK;
+}
+
 // ------------------------------------------------------------------ power iteration kernels (FP64)
 
 __device__ __forceinline__ double level_elem(const LevelDev& L, int64_t j, int64_t n) {
@@ -373,10 +442,6 @@ __global__ void k_fill(double* p, int64_t n, double v) {
 
 // ------------------------------------------------------------------------------ host side
 
-static int grid_for(int64_t n, int threads = 256) {
-  int64_t g = (n + threads - 1) / threads;
-  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 1 << 20);
-}
 
 static int alloc(void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
@@ -414,6 +479,18 @@ static void level_rounding(const lasso_dict* d, const HostLevel& h, bool vt_doub
     L.gam_tight = L.gam_corr;
     L.res_model = RES_FOLD;
     L.gam_res = gamma_n(f8 ? 7.0 : 6.0, U32);
+    return;
+  }
+  if (tc && h.kind == LK_F32) {
+    // split exact level on the tensor cores: 3 (N + N / 16) BF16 products accumulated (the
+    // three partial products summed in one accumulator), then the FP32 store; the sum of
+    // |a1 r1| + |a1 r2| + |a2 r1| is <= (1 + 2^-7)^2 kappa_j ||rho||.  The certificate atoms are
+    // recomputed from the FP32 data with error-free products (gam_tight), the residual as for
+    // the FP32 level.
+    L.gam_corr = 1.02 * gamma_n(3.0 * (N + N / 16.0) + 3.0, TC_U_BF16) + stage;
+    L.gam_tight = 2.0 * gamma_n(2.0 * nl, U32) * gamma_n(2.0 * nl, U32) + stage;
+    L.res_model = RES_DOT2;
+    L.gam_res = vt_double ? U32 : 0.0;
     return;
   }
   switch (h.kind) {
@@ -476,6 +553,10 @@ static void free_level(HostLevel& h) {
     cudaFree(h.kappa32);
     cudaFree(h.eps32);
   }
+  cudaFree(h.split1);
+  cudaFree(h.split2);
+  cudaFree(h.e3);
+  cudaFree(h.epsr32_split);
   h = HostLevel();
 }
 
@@ -493,6 +574,17 @@ static int ensure_level_f32(const lasso_dict* d, const HostLevel& hc, bool vt_do
     k_round_up_f32<<<grid_for(d->K), 256>>>(h.eps, nullptr, 0.0, d->K, h.eps32);
     LASSO_CUDA_TRY(cudaGetLastError());
     LASSO_CUDA_TRY(cudaDeviceSynchronize());
+  }
+  if (tc && h.kind == LK_F32) {
+    // split tensor-core exact level: eps_j + gam_corr kappa_j + ||a_j - a1_j - a2_j||
+    if (!h.split1 || !h.e3) return LASSO_ERR_INVALID_ARG;
+    if (!h.epsr32_split) {
+      LASSO_CUDA_TRY(cudaMalloc(&h.epsr32_split, d->K * sizeof(float)));
+      k_round_up3_f32<<<grid_for(d->K), 256>>>(h.eps, h.kappa, L.gam_corr, h.e3, d->K, h.epsr32_split);
+      LASSO_CUDA_TRY(cudaGetLastError());
+      LASSO_CUDA_TRY(cudaDeviceSynchronize());
+    }
+    return LASSO_OK;
   }
   float*& dst = h.epsr32[(vt_double ? 1 : 0) + (tc ? 2 : 0)];
   if (dst) return LASSO_OK;
@@ -516,13 +608,27 @@ LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double,
   L.kappa = h.kappa;
   L.atnorm = h.atnorm;
   L.rc = h.rc;
-  tc = tc && (h.kind == LK_BF16 || h.kind == LK_FP8);
+  const bool split = tc && h.kind == LK_F32 && !vt_double && h.split1 != nullptr;
+  tc = (tc && (h.kind == LK_BF16 || h.kind == LK_FP8)) || split;
   L.tc = tc ? 1 : 0;
+  L.split = split ? 1 : 0;
+  L.c2 = split ? h.c2 : 0.0;
+  if (split) {
+    // the plain FP32 bounds serve the fast checks outside the bulk pass (full-dictionary check)
+    LevelDev Ls = L;
+    Ls.tc = 0;
+    Ls.split = 0;
+    level_rounding(d, h, vt_double, false, Ls);
+    if (h.eps && ensure_level_f32(d, h, vt_double, false, Ls) == LASSO_OK)
+      L.epsr32_simt = h.epsr32[vt_double ? 1 : 0];
+  }
   level_rounding(d, h, vt_double, tc, L);
   if (h.eps && ensure_level_f32(d, h, vt_double, tc, L) == LASSO_OK) {
-    L.epsr32 = h.epsr32[(vt_double ? 1 : 0) + (tc ? 2 : 0)];
+    L.epsr32 = split ? h.epsr32_split : h.epsr32[(vt_double ? 1 : 0) + (tc ? 2 : 0)];
     L.kappa32 = h.kappa32;
     L.eps32 = h.eps32;
+    if (!split) L.epsr32_simt = L.epsr32;
+    if (split && !L.epsr32_simt) L.epsr32 = nullptr;
   } else if (h.eps) {
     L.epsr32 = nullptr;   // build_dict_dev rejects a level without its FP32 bounds
   }
@@ -549,13 +655,16 @@ int ensure_rung64(lasso_dict* d) {
   for (auto& e : h.epsr32) e = nullptr;
   h.kappa32 = nullptr;
   h.eps32 = nullptr;
+  h.split1 = h.split2 = nullptr;
+  h.e3 = nullptr;
+  h.epsr32_split = nullptr;
   return LASSO_OK;
 }
 
 static bool dict_trace() { return getenv("LASSO_TRACE_STEPS") != nullptr; }
 
 int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order,
-                   bool tc_levels) {
+                   bool tc_levels, bool tc_exact) {
   if (dict_trace()) fprintf(stderr, "[lasso trace] build_dict_dev: enter\n");
   memset(out, 0, sizeof(*out));
   out->N = (int)d->N;
@@ -589,8 +698,13 @@ int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<con
   if ((int)lv.size() > MAX_LEVELS) return LASSO_ERR_INVALID_ARG;
   out->n_levels = (int)lv.size();
   const bool vt_double = final_fp64 || d->exact_kind == LK_F64;
+  if (tc_exact && !vt_double && d->exact_kind == LK_F32) {
+    int rc = ensure_split(d);
+    if (rc) return rc;
+  }
   for (size_t i = 0; i < lv.size(); ++i) {
-    out->lv[i] = make_level_dev(d, *lv[i], vt_double, tc_levels);
+    const bool is_exact = lv[i] == &d->exact;
+    out->lv[i] = make_level_dev(d, *lv[i], vt_double, is_exact ? (tc_exact && !vt_double) : tc_levels);
     if (!out->lv[i].epsr32) return LASSO_ERR_CUDA;
   }
   if (order) *order = lv;

@@ -21,6 +21,12 @@ struct HostLevel {
   float* epsr32[4] = {nullptr, nullptr, nullptr, nullptr};   // per (iterate precision, tensor cores)
   float* kappa32 = nullptr;
   float* eps32 = nullptr;      // eps_j rounded up to FP32
+  // exact FP32 level only: BF16 split a = a1 + a2 + e3 for the tensor-core exact level
+  void* split1 = nullptr;
+  void* split2 = nullptr;
+  double* e3 = nullptr;        // ||a_j - a1_j - a2_j|| (rounded up)
+  float* epsr32_split = nullptr;
+  double c2 = 0.0;             // max_j ||a2_j|| / kappa_j (rounded up)
   float* dscale = nullptr;     // Kronecker d_j as FP32
   double u = U32, gam_corr = 0.0, gam_res = 0.0, rc = 1.0;
   bool rc_set = false;
@@ -57,9 +63,12 @@ namespace lasso {
 // Level descriptor for kernels.  vt_double: the solve iterates in FP64 (affects the roundings).
 LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double = false, bool tc = false);
 // All levels of a solve, coarsest first, exact (or the FP64 rung) last.  tc_levels: run the
-// batched BF16 / FP8 correlations on the tensor cores.
+// batched BF16 / FP8 correlations on the tensor cores; tc_exact: the exact FP32 level too, in
+// its split BF16 form.
 int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order,
-                   bool tc_levels = false);
+                   bool tc_levels = false, bool tc_exact = false);
+// BF16 split of the exact FP32 level and its bounds (computed once).
+int ensure_split(lasso_dict* d);
 int ensure_rung64(lasso_dict* d);
 int dict_prepare(lasso_dict* d, double L_override);
 

@@ -47,7 +47,7 @@ struct Workspace {
   double* part_res = nullptr;        // B x nrb x 2
   double* part_corr = nullptr;       // B x nch x 2
   int32_t* offsets = nullptr;        // B + 1
-  int32_t* counters = nullptr;       // [0] done count
+  int32_t* counters = nullptr;       // [0] done count, [8 + l] signals on tensor-core level l
   double* alg_bytes = nullptr;       // [6] algorithmic bytes per kernel kind
   SigState* st = nullptr;
   // Kronecker scratch
@@ -55,8 +55,11 @@ struct Workspace {
   float* AZ = nullptr;               // B x ldN
   float* Xd = nullptr;               // B x K
   float* Tk = nullptr;               // B x R x max(K1 N2, N1 K2)
-  void* rq[MAX_LEVELS] = {nullptr};  // tensor-core levels: quantised residuals (B x ldN)
+  void* rq[MAX_LEVELS] = {nullptr};  // tensor-core levels: quantised residuals (B slots x ldN)
+  void* rq2[MAX_LEVELS] = {nullptr}; // split exact level: second BF16 part of the residuals
   float* rsig[MAX_LEVELS] = {nullptr};
+  int32_t* tc_slot = nullptr;        // MAX_LEVELS x B: slot of signal b on level l (or -1)
+  int32_t* tc_list = nullptr;        // MAX_LEVELS x B: signal in slot s of level l
   int* tc_err = nullptr;
   int32_t* h_counters = nullptr;     // pinned
   cudaStream_t stream = nullptr;     // used when the caller passes the legacy default stream
@@ -71,8 +74,11 @@ void free_ws(Workspace* w) {
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < MAX_LEVELS; ++l) {
     cudaFree(w->rq[l]);
+    cudaFree(w->rq2[l]);
     cudaFree(w->rsig[l]);
   }
+  cudaFree(w->tc_slot);
+  cudaFree(w->tc_list);
   cudaFree(w->tc_err);
   cudaFreeHost(w->h_counters);
   if (w->stream) cudaStreamDestroy(w->stream);
@@ -133,6 +139,8 @@ static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
   rc |= ws_alloc((void**)&w->counters, 64);
   rc |= ws_alloc((void**)&w->alg_bytes, 16 * sizeof(double));   // [0,6) bytes, [8,16) atom-passes per level
   rc |= ws_alloc((void**)&w->st, (size_t)B * sizeof(SigState));
+  rc |= ws_alloc((void**)&w->tc_slot, (size_t)MAX_LEVELS * B * 4);
+  rc |= ws_alloc((void**)&w->tc_list, (size_t)MAX_LEVELS * B * 4);
   if (d->is_kron) {
     const size_t tk = (size_t)B * d->R * std::max<int64_t>((int64_t)d->K1 * d->N2, (int64_t)d->N1 * d->K2);
     rc |= ws_alloc((void**)&w->Gfull, BK * 4);
@@ -182,6 +190,8 @@ struct PassArgs {
   float* AZ;
   float* Xd;
   float* Tk;
+  int32_t* tc_slot;
+  int32_t* tc_list;
   int64_t K, ldN;
   int nrb, nch;
 };
@@ -230,6 +240,8 @@ static void fill_pass_args(PassArgs<VT>& pa, Workspace* w, const lasso_dict* d) 
   pa.AZ = w->AZ;
   pa.Xd = w->Xd;
   pa.Tk = w->Tk;
+  pa.tc_slot = w->tc_slot;
+  pa.tc_list = w->tc_list;
   pa.K = d->K;
   pa.ldN = d->ldN;
   pa.nrb = w->nrb;
@@ -333,6 +345,39 @@ __global__ void k_schedule(PassArgs<VT> a) {
   if (threadIdx.x == 0) {
     a.offsets[B] = carry;
     a.counters[0] = done_total;
+  }
+  // slots of the live signals on each tensor-core level: the rows of that level's quantised
+  // residual operand, so the batched GEMM covers only ceil(count / 256) signal tiles
+  for (int l = 0; l < a.dd.n_levels; ++l) {
+    if (!a.dd.lv[l].tc) continue;
+    __syncthreads();
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < B; base += blockDim.x) {
+      const int b = base + threadIdx.x;
+      const bool on = b < B && !a.st[b].done && a.st[b].level == l;
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (lane == 0) sh_sum[wid] = __popc(bal);
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        int x = (int)threadIdx.x < nw ? sh_sum[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, x, o);
+          if ((int)threadIdx.x >= o) x += t;
+        }
+        sh_sum[threadIdx.x] = x;   // inclusive over warps
+      }
+      __syncthreads();
+      const int slot = carry + (wid ? sh_sum[wid - 1] : 0) + __popc(bal & ((1u << lane) - 1u));
+      if (b < B) a.tc_slot[(int64_t)l * B + b] = on ? slot : -1;
+      if (on) a.tc_list[(int64_t)l * B + slot] = b;
+      __syncthreads();
+      if (threadIdx.x == 0) carry += sh_sum[nw - 1];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a.counters[8 + l] = carry;
   }
 }
 
@@ -730,117 +775,78 @@ __device__ __forceinline__ int item_signal(const int* __restrict__ offsets, int 
 // The correlation pass for FP32 iterates: g_j = a~_j^T rho^ over the preserved list, fused with
 // the FISTA update of those coefficients and with the two maxima of the pass,
 // max_j (|g_j| + eps_j ||rho^||) (upper bound, stable scaling) and max_j |g_j|.
-// Each block takes a contiguous range of (signal, chunk) items, so the signal's scalars are read
-// once per signal; each warp takes chunk / 8 consecutive positions of an item: lane l holds
-// position l (index, x, z and bound loaded up front), the warp forms the dot products two atoms
-// at a time, and the lanes then update their own coefficients in parallel.  The maxima go to
-// the signal's state with atomicMax on FP32 bit patterns (non-negative values), so no block
-// barrier is needed.  Every per-atom operation is FP32; the bounds use directed rounding.
+// Persistent grid over (signal, chunk) items; the eight warps of a block share an item, each
+// warp forming two dot products at a time (lanes 0 and 1 then update the two coefficients).
+// Levels whose correlations come from a batched product (tensor cores, Kronecker) only run the
+// update, one coefficient per thread.  The signal's pass scalars are FP32 copies prepared by
+// k_residual; the maxima go to the signal's state with atomicMax on FP32 bit patterns
+// (non-negative values).  Every per-atom operation is FP32; the bounds use directed rounding.
 template <typename VT>
-__global__ void __launch_bounds__(CORR_THREADS, 4) k_corr_pass(PassArgs<VT> a) {
+__global__ void __launch_bounds__(CORR_THREADS) k_corr_pass(PassArgs<VT> a) {
   static_assert(sizeof(VT) == 4, "FP32 iterates only");
   constexpr int NW = CORR_THREADS / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int B = a.sp.B;
   const int total = a.offsets[B];
-  const int CH = a.sp.chunk;
-  const int PW = CH / NW;
-  const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int i0 = (int)blockIdx.x * per, i1 = min(total, i0 + per);
-  if (i0 >= i1) return;
   const int ldN = (int)a.ldN;
+  const int CH = a.sp.chunk;
   const float ga_fac = 1.0000004f;   // >= 1 + 3 u32, rounded up
   const float inv_Lf = (float)a.sp.inv_L;
   const bool fista = a.sp.algo == LASSO_FISTA;
   float bytes = 0.f;
-  int b = -1, b_first = 0, b_end = 0;
-  int lvl = 0, n_kept = 0;
-  bool from_full = false, tc = false;
-  float nrho_f = 0.f, thr_f = 0.f, beta_f = 0.f, dq_f = 0.f;
-  const int32_t* kp = nullptr;
-  VT *X = nullptr, *Z = nullptr, *G = nullptr;
-  const VT* rho = nullptr;
-  float m1 = 0.f, m2 = 0.f;
-  for (int item = i0; item < i1; ++item) {
-    if (item >= b_end) {
-      if (b >= 0) {
-        // flush the previous signal's maxima
-        m1 = warp_max_f(m1);
-        m2 = warp_max_f(m2);
-        if (lane == 0) {
-          atomicMax(&a.st[b].pm1, __float_as_uint(m1));
-          atomicMax(&a.st[b].pm2, __float_as_uint(m2));
-        }
-      }
-      b = item_signal(a.offsets, b + 1, B - 1, item);
-      b_first = a.offsets[b];
-      b_end = a.offsets[b + 1];
-      const SigState& s = a.st[b];
-      lvl = s.level;
-      n_kept = s.n_kept;
-      nrho_f = s.nrho_ru;
-      thr_f = s.thr_f;
-      beta_f = s.beta_f;
-      const LevelDev& L = a.dd.lv[lvl];
-      tc = L.tc != 0;
-      from_full = L.kind == LK_KRON || tc;
-      dq_f = tc ? __double2float_ru(s.dq * 1.001) : 0.f;
-      kp = kept_of(a, b, s.parity);
-      X = a.X + (int64_t)b * a.K;
-      Z = a.Z + (int64_t)b * a.K;
-      G = a.G + (int64_t)b * a.K;
-      rho = a.Rho + (int64_t)b * a.ldN;
-      m1 = 0.f;
-      m2 = 0.f;
-    }
-    if (a.alg_bytes && !from_full && item == b_first && wid == 0 && lane == 0) bytes += (float)a.dd.N * sizeof(VT);
-    const LevelDev& L = a.dd.lv[lvl];
-    const int q0 = (item - b_first) * CH + wid * PW;
-    const int cnt = min(PW, n_kept - q0);
-    if (cnt <= 0) continue;
-    const bool mine = lane < cnt;
-    const int pos = q0 + lane;
-    const int32_t j = mine ? kp[pos] : 0;
-    float xj = 0.f, zj = 0.f, er = 0.f, kq = 0.f, g = 0.f;
-    if (mine) {
-      xj = (float)X[j];
-      zj = (float)Z[j];
-      er = L.epsr32[j];
-      if (dq_f > 0.f) kq = L.kappa32[j];
-      if (from_full) g = a.Gfull[(int64_t)b * a.K + j];
-    }
-    if (!from_full) {
-      for (int q = 0; q < cnt; q += 2) {
-        const int j0 = __shfl_sync(0xffffffffu, j, q);
-        const int j1 = __shfl_sync(0xffffffffu, j, q + 1 < cnt ? q + 1 : q);
-        float g0, g1;
-        warp_atom_dot2_fast<VT>(L, j0, j1, ldN, rho, lane, g0, g1);
-        g = lane == q ? g0 : (lane == q + 1 ? g1 : g);
-      }
-      if (a.alg_bytes && lane == 0)
-        bytes += (float)cnt * ((float)a.dd.N * level_elem_bytes(L.kind) + 4.f + 5.f * sizeof(VT));
-    }
-    if (mine) {
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int b = item_signal(a.offsets, 0, B - 1, item);
+    const int chunk = item - a.offsets[b];
+    const SigState& s = a.st[b];
+    const LevelDev& L = a.dd.lv[s.level];
+    const int p0 = chunk * CH, p1 = min(s.n_kept, p0 + CH);
+    const VT* rho = a.Rho + (int64_t)b * a.ldN;
+    const float nrho_f = s.nrho_ru, thr_f = s.thr_f, beta_f = s.beta_f;
+    const bool from_full = L.kind == LK_KRON || L.tc;
+    const float dq_f = L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
+    const int32_t* kp = kept_of(a, b, s.parity);
+    VT* X = a.X + (int64_t)b * a.K;
+    VT* Z = a.Z + (int64_t)b * a.K;
+    VT* G = a.G + (int64_t)b * a.K;
+    float m1 = 0.f, m2 = 0.f;
+    auto update = [&](int pos, int32_t j, float g) {
       const float ag = fabsf(g);
-      float ub = __fmaf_ru(er, nrho_f, __fmul_ru(ag, ga_fac));
-      if (dq_f > 0.f) ub = __fmaf_ru(kq, dq_f, ub);
+      float ub = __fmaf_ru(L.epsr32[j], nrho_f, __fmul_ru(ag, ga_fac));
+      if (dq_f > 0.f) ub = __fmaf_ru(L.kappa32[j], dq_f, ub);
       m1 = fmaxf(m1, ub);
       m2 = fmaxf(m2, ag);
+      const float xj = (float)X[j], zj = (float)Z[j];
       const float v = __fmaf_rn(g, inv_Lf, zj);
       const float xn = v > thr_f ? v - thr_f : (v < -thr_f ? v + thr_f : 0.f);
       const float zn = fista ? __fmaf_rn(beta_f, xn - xj, xn) : xn;
       X[j] = (VT)xn;
       Z[j] = (VT)zn;
       G[pos] = (VT)g;
+    };
+    if (from_full) {
+      for (int pos = p0 + (int)threadIdx.x; pos < p1; pos += CORR_THREADS) {
+        const int32_t j = kp[pos];
+        update(pos, j, a.Gfull[(int64_t)b * a.K + j]);
+      }
+    } else {
+      for (int base = p0 + wid; base < p1; base += 2 * NW) {
+        const bool two = base + NW < p1;
+        const int32_t j0 = kp[base], j1 = two ? kp[base + NW] : j0;
+        float g0, g1;
+        warp_atom_dot2_fast<VT>(L, j0, j1, ldN, rho, lane, g0, g1);
+        if (lane == 0) update(base, j0, g0);
+        else if (lane == 1 && two) update(base + NW, j1, g1);
+        if (a.alg_bytes && lane == 0)
+          bytes += (two ? 2.f : 1.f) * ((float)a.dd.N * level_elem_bytes(L.kind) + 4.f + 5.f * sizeof(VT));
+      }
+      if (a.alg_bytes && chunk == 0 && wid == 0 && lane == 0) bytes += (float)a.dd.N * sizeof(VT);
     }
+    m1 = warp_max_f(m1);
+    m2 = warp_max_f(m2);
+    if (lane == 0 && m1 > 0.f) atomicMax(&a.st[b].pm1, __float_as_uint(m1));
+    if (lane == 0 && m2 > 0.f) atomicMax(&a.st[b].pm2, __float_as_uint(m2));
   }
-  m1 = warp_max_f(m1);
-  m2 = warp_max_f(m2);
-  if (lane == 0) {
-    atomicMax(&a.st[b].pm1, __float_as_uint(m1));
-    atomicMax(&a.st[b].pm2, __float_as_uint(m2));
-    if (a.alg_bytes && bytes > 0.f) atomicAdd(&a.alg_bytes[1], (double)bytes);
-  }
+  if (a.alg_bytes && lane == 0 && bytes > 0.f) atomicAdd(&a.alg_bytes[1], (double)bytes);
 }
 
 template <typename VT>
@@ -982,7 +988,9 @@ __global__ void __launch_bounds__(SCREEN_THREADS, 3) k_screen(PassArgs<VT> a) {
       const double T = sc[11], nrho = sqrt(sc[8]);
       const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
       const float T_f = __double2float_rd(T);
-      const float gn_f = __double2float_ru(L.gam_corr * nrho);
+      // |g^_j - a_j^T rho| <= epsr_j ||rho|| (+ kappa_j dq for a quantised operand) + 3 u |g^_j|
+      const float nr_f = __double2float_ru(nrho);
+      const float dq_f = L.tc ? __double2float_ru(sp->dq * 1.001) : 0.f;
       double wm = 0.0;
       for (int base = wid * 32; base < n_kept; base += SCREEN_THREADS) {
         const int pos = base + lane;
@@ -990,7 +998,8 @@ __global__ void __launch_bounds__(SCREEN_THREADS, 3) k_screen(PassArgs<VT> a) {
         bool cand = false;
         if (pos < n_kept) {
           j = kp[pos];
-          const float ub = __fmaf_ru(L.kappa32[j], gn_f, __fmul_ru(fabsf((float)G[pos]), 1.0000004f));
+          float ub = __fmaf_ru(L.epsr32[j], nr_f, __fmul_ru(fabsf((float)G[pos]), 1.0000004f));
+          if (dq_f > 0.f) ub = __fmaf_ru(L.kappa32[j], dq_f, ub);
           cand = ub > T_f;
         }
         unsigned m = __ballot_sync(0xffffffffu, cand);
@@ -1370,7 +1379,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_full_check(PassArgs<VT> a) {
     for (int64_t j = j0 + wid; j < j1; j += CORR_THREADS / 32) {
       if (mk[j]) continue;   // warp-uniform: every lane reads the same flag
       const float g = (float)warp_atom_dot_fast<VT>(L, j, (int)a.ldN, rho, lane);
-      m = fmaxf(m, __fmaf_ru(L.epsr32[j], nrho_f, __fmul_ru(fabsf(g), 1.0000004f)));
+      m = fmaxf(m, __fmaf_ru(L.epsr32_simt[j], nrho_f, __fmul_ru(fabsf(g), 1.0000004f)));
     }
     if (lane == 0) s_m[wid] = m;
     __syncthreads();
@@ -1431,62 +1440,118 @@ __global__ void k_full_finish(PassArgs<VT> a) {
 
 // ------------------------------------------------------------------ tensor-core operand
 
-// Quantise rho^ of the signals on a tensor-core level (BF16, or E4M3 with the per-signal scale
-// sigma = max |rho| / 448) and record dq = ||rho^ - sigma r^|| exactly: the correlation of the
-// quantised operand differs from a~_j^T rho^ by at most ||a~_j|| dq, which the bounds add.
+// Quantise rho^ of the signals on a tensor-core level into their slot rows of the GEMM operand
+// (BF16; E4M3 with the per-signal scale sigma = max |rho| / 448; or the split r1 + r2 of two
+// BF16 parts for the split exact level) and bound dq >= ||rho^ - (quantised rho^)||: the
+// correlation of the quantised operand differs from a~_j^T rho^ by at most kappa_j dq, which the
+// bounds add.  The split level adds c2 ||r2|| for the product a2^T r2 it leaves out.  FP32
+// iterates: exact differences (BF16, split) or one rounding (E4M3), squares summed upward.
 template <typename VT>
 __global__ void __launch_bounds__(256) k_quant_rho(PassArgs<VT> a, int lvl, int fp8) {
   const int b = blockIdx.x;
-  __shared__ int s_go;
+  const int B = a.sp.B;
+  const int slot = a.tc_slot[(int64_t)lvl * B + b];
+  if (slot < 0) return;
   __shared__ float s_max[8];
-  __shared__ double s_sum[8];
+  __shared__ double s_sum[2][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_go = !a.st[b].done && a.st[b].level == lvl;
-  __syncthreads();
-  if (!s_go) return;
   const LevelDev& L = a.dd.lv[lvl];
   const VT* rho = a.Rho + (int64_t)b * a.ldN;
   const int N = a.dd.N;
-  float m = 0.f;
-  for (int n = threadIdx.x; n < N; n += 256) m = fmaxf(m, fabsf((float)rho[n]));
-#pragma unroll
-  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) s_max[wid] = m;
-  __syncthreads();
-  float mx = 0.f;
-  for (int w = 0; w < 8; ++w) mx = fmaxf(mx, s_max[w]);
-  const float sg = fp8 ? (mx > 0.f ? mx / 448.f : 1.f) : 1.f;
-  double dq2 = 0.0;
+  const int64_t row = (int64_t)slot * a.ldN;
+  float sg = 1.f;
   if (fp8) {
-    uint8_t* out = reinterpret_cast<uint8_t*>(L.rq) + (int64_t)b * a.ldN;
-    for (int n = threadIdx.x; n < a.ldN; n += 256) {
-      const double r = n < N ? (double)rho[n] : 0.0;
-      const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fdiv_rn((float)r, sg), __NV_SATFINITE, __NV_E4M3);
-      out[n] = q;
-      __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
-      const double e = r - (double)__half2float(__half(hr)) * (double)sg;
-      dq2 = fma(e, e, dq2);
-    }
-  } else {
-    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(L.rq) + (int64_t)b * a.ldN;
-    for (int n = threadIdx.x; n < a.ldN; n += 256) {
-      const double r = n < N ? (double)rho[n] : 0.0;
-      const __nv_bfloat16 q = __float2bfloat16_rn((float)r);
-      out[n] = q;
-      const double e = r - (double)__bfloat162float(q);
-      dq2 = fma(e, e, dq2);
-    }
+    float m = 0.f;
+    for (int n = threadIdx.x; n < N; n += 256) m = fmaxf(m, fabsf((float)rho[n]));
+    m = warp_max_f(m);
+    if (lane == 0) s_max[wid] = m;
+    __syncthreads();
+    float mx = 0.f;
+    for (int w = 0; w < 8; ++w) mx = fmaxf(mx, s_max[w]);
+    sg = mx > 0.f ? mx / 448.f : 1.f;
   }
-  dq2 = warp_sum(dq2);
-  if (lane == 0) s_sum[wid] = dq2;
+  double dq2 = 0.0, r22 = 0.0;
+  if constexpr (sizeof(VT) == 8) {
+    // FP64 iterates: differences in FP64
+    if (fp8) {
+      uint8_t* out = reinterpret_cast<uint8_t*>(L.rq) + row;
+      for (int n = threadIdx.x; n < a.ldN; n += 256) {
+        const double r = n < N ? (double)rho[n] : 0.0;
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fdiv_rn((float)r, sg), __NV_SATFINITE, __NV_E4M3);
+        out[n] = q;
+        __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+        const double e = r - (double)__half2float(__half(hr)) * (double)sg;
+        dq2 = fma(e, e, dq2);
+      }
+    } else {
+      __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(L.rq) + row;
+      for (int n = threadIdx.x; n < a.ldN; n += 256) {
+        const double r = n < N ? (double)rho[n] : 0.0;
+        const __nv_bfloat16 q = __float2bfloat16_rn((float)r);
+        out[n] = q;
+        const double e = r - (double)__bfloat162float(q);
+        dq2 = fma(e, e, dq2);
+      }
+    }
+    dq2 = warp_sum(dq2);
+  } else {
+    float acc = 0.f, acc2 = 0.f;
+    if (fp8) {
+      uint8_t* out = reinterpret_cast<uint8_t*>(L.rq) + row;
+      for (int n = threadIdx.x; n < a.ldN; n += 256) {
+        const float r = n < N ? (float)rho[n] : 0.f;
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fdiv_rn(r, sg), __NV_SATFINITE, __NV_E4M3);
+        out[n] = q;
+        __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+        // one rounding of r - q sg; |fl(e)| (1 + 2^-23) bounds the exact difference
+        const float e = __fmul_ru(fabsf(__fmaf_rn(-__half2float(__half(hr)), sg, r)), 1.00000012f);
+        acc = __fmaf_ru(e, e, acc);
+      }
+    } else if (L.split) {
+      __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(L.rq) + row;
+      __nv_bfloat16* out2 = reinterpret_cast<__nv_bfloat16*>(L.rq2) + row;
+      for (int n = threadIdx.x; n < a.ldN; n += 256) {
+        const float r = n < N ? (float)rho[n] : 0.f;
+        const __nv_bfloat16 q1 = __float2bfloat16_rn(r);
+        const float d1 = __fsub_rn(r, __bfloat162float(q1));     // exact
+        const __nv_bfloat16 q2 = __float2bfloat16_rn(d1);
+        const float r2 = __bfloat162float(q2);
+        const float d2 = __fsub_rn(d1, r2);                       // exact
+        out[n] = q1;
+        out2[n] = q2;
+        acc = __fmaf_ru(d2, d2, acc);
+        acc2 = __fmaf_ru(r2, r2, acc2);
+      }
+    } else {
+      __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(L.rq) + row;
+      for (int n = threadIdx.x; n < a.ldN; n += 256) {
+        const float r = n < N ? (float)rho[n] : 0.f;
+        const __nv_bfloat16 q = __float2bfloat16_rn(r);
+        out[n] = q;
+        const float e = __fsub_rn(r, __bfloat162float(q));        // exact
+        acc = __fmaf_ru(e, e, acc);
+      }
+    }
+    dq2 = (double)warp_sum_ru(acc);
+    r22 = (double)warp_sum_ru(acc2);
+  }
+  if (lane == 0) {
+    s_sum[0][wid] = dq2;
+    s_sum[1][wid] = r22;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += s_sum[w];
-    a.st[b].dq = sqrt(t) * (1.0 + 1e-12);
-    L.rsig[b] = sg;
-    // algorithmic work of the batched correlation of this signal: 2 N K flops
-    if (a.alg_bytes) atomicAdd(&a.alg_bytes[5], 2.0 * (double)a.dd.N * (double)a.K);
+    double t = 0.0, t2 = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      t += s_sum[0][w];
+      t2 += s_sum[1][w];
+    }
+    double dq = sqrt(t) * (1.0 + 1e-12);
+    if (L.split) dq += L.c2 * sqrt(t2) * (1.0 + 1e-12);
+    a.st[b].dq = dq;
+    if (fp8) L.rsig[b] = sg;
+    // algorithmic work of the batched correlation of this signal: 2 N K flops per product
+    if (a.alg_bytes) atomicAdd(&a.alg_bytes[5], (L.split ? 3.0 : 1.0) * 2.0 * (double)a.dd.N * (double)a.K);
   }
 }
 
@@ -1774,7 +1839,8 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   if (ev) cudaEventRecordWithFlags(ev[7], st, cudaEventRecordExternal);
   for (const TcJob& j : tc) {
     k_quant_rho<VT><<<B, 256, 0, st>>>(pa, j.lvl, j.fp8);
-    tc_launch_corr(j.ops, pa.K, B, pa.ldN, j.scale, j.rsig, pa.st, j.lvl, pa.Gfull, tc_err, st);
+    tc_launch_corr(j.ops, pa.K, B, pa.ldN, j.scale, j.rsig, pa.tc_list + (int64_t)j.lvl * B, pa.counters + 8 + j.lvl,
+                   pa.Gfull, tc_err, st);
   }
   if (ev) cudaEventRecordWithFlags(ev[8], st, cudaEventRecordExternal);
   if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
@@ -1806,34 +1872,39 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   PassArgs<VT> pa;
   memset(&pa, 0, sizeof(pa));
   std::vector<const HostLevel*> order;
-  bool want_tc = o.tensor_cores && B >= TC_BN && d->K >= TC_BM;
-  if (want_tc) {
-    bool any = false;
-    for (auto& h : d->approx) any |= h.kind == LK_BF16 || h.kind == LK_FP8;
-    want_tc = any;
-  }
-  int rc = build_dict_dev(d, o.final_fp64 != 0, &pa.dd, &order, want_tc);
+  const bool tc_batch = o.tensor_cores && B >= TC_BN && d->K >= TC_BM;
+  bool any_approx = false;
+  for (auto& h : d->approx) any_approx |= h.kind == LK_BF16 || h.kind == LK_FP8;
+  const bool want_tc = tc_batch && any_approx;
+  const bool tc_exact = tc_batch && o.tc_exact && sizeof(VT) == 4 && !o.final_fp64 && d->exact_kind == LK_F32;
+  int rc = build_dict_dev(d, o.final_fp64 != 0, &pa.dd, &order, want_tc, tc_exact);
   if (rc) return rc;
   std::vector<TcJob> tc_jobs;
   for (int l = 0; l < pa.dd.n_levels; ++l) {
     LevelDev& L = pa.dd.lv[l];
     if (!L.tc) continue;
     const int fp8 = L.kind == LK_FP8;
-    const size_t bytes = (size_t)w->B * d->ldN * (fp8 ? 1 : 2);
     if (!w->rq[l]) {
       if (ws_alloc(&w->rq[l], (size_t)w->B * d->ldN * 2) || ws_alloc((void**)&w->rsig[l], (size_t)w->B * 4))
         return LASSO_ERR_NOMEM;
       LASSO_CUDA_TRY(cudaMemset(w->rq[l], 0, (size_t)w->B * d->ldN * 2));
     }
-    (void)bytes;
+    if (L.split && !w->rq2[l]) {
+      if (ws_alloc(&w->rq2[l], (size_t)w->B * d->ldN * 2)) return LASSO_ERR_NOMEM;
+      LASSO_CUDA_TRY(cudaMemset(w->rq2[l], 0, (size_t)w->B * d->ldN * 2));
+    }
     L.rq = w->rq[l];
+    L.rq2 = L.split ? w->rq2[l] : nullptr;
     L.rsig = w->rsig[l];
     TcJob job;
     job.lvl = l;
     job.fp8 = fp8;
     job.scale = fp8 ? L.scale : nullptr;
     job.rsig = fp8 ? L.rsig : nullptr;
-    rc = tc_make_operands(L.data, d->K, L.rq, B, d->ldN, fp8, &job.ops);
+    if (L.split)
+      rc = tc_make_operands(d->exact.split1, d->exact.split2, d->K, L.rq, L.rq2, B, d->ldN, 0, &job.ops);
+    else
+      rc = tc_make_operands(L.data, nullptr, d->K, L.rq, nullptr, B, d->ldN, fp8, &job.ops);
     if (rc) return rc;
     tc_jobs.push_back(job);
   }
@@ -2032,6 +2103,7 @@ extern "C" void lasso_opts_default(lasso_opts* o) {
   o->time_limit_s = 0.0;
   o->profile = 0;
   o->full_gap = 1;
+  o->tc_exact = 0;
 }
 
 static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {

@@ -106,13 +106,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 template <int FP8>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb, int64_t K, int64_t B,
-          int nkb, const float* __restrict__ scale, const float* __restrict__ sigma, const SigState* __restrict__ st,
-          int lvl, float* __restrict__ Gfull, int* __restrict__ err) {
+k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb,
+          const __grid_constant__ CUtensorMap tma2, const __grid_constant__ CUtensorMap tmb2, int64_t K, int64_t B,
+          int nkb, int nphase, const float* __restrict__ scale, const float* __restrict__ sigma,
+          const int* __restrict__ list, const int* __restrict__ count, float* __restrict__ Gfull,
+          int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
-  __shared__ int s_active, s_fail;
+  __shared__ int s_fail;
   __shared__ uint8_t s_on[TC_BN];
   __shared__ float s_sigma[TC_BN];
+  __shared__ int s_sig[TC_BN];
   __shared__ uint32_t s_tmem;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;                                    // TC_STAGES x 16 KB
@@ -125,26 +128,19 @@ k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUten
   const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
   const int64_t n0 = (int64_t)blockIdx.y * TC_BN;
 
-  // ---- which signals of the tile are on this level (uniform early exit)
-  if (threadIdx.x == 0) {
-    s_active = 0;
-    s_fail = 0;
-  }
-  __syncthreads();
+  // ---- the tile's signal slots (uniform early exit past the count)
+  const int64_t nslots = count ? (int64_t)*count : B;
+  if (n0 >= nslots) return;
+  if (threadIdx.x == 0) s_fail = 0;
   for (int i = threadIdx.x; i < TC_BN; i += TC_THREADS) {
-    const int64_t b = n0 + i;
-    uint8_t on = 0;
-    float sg = 0.f;
-    if (b < B && !st[b].done && st[b].level == lvl) {
-      on = 1;
-      sg = sigma ? sigma[b] : 1.f;
-      atomicOr(&s_active, 1);
-    }
-    s_on[i] = on;
-    s_sigma[i] = sg;
+    const int64_t slot = n0 + i;
+    const bool on = slot < nslots;
+    const int b = on ? (list ? list[slot] : (int)slot) : 0;
+    s_on[i] = on ? 1 : 0;
+    s_sig[i] = b;
+    s_sigma[i] = on ? (sigma ? sigma[b] : 1.f) : 0.f;
   }
   __syncthreads();
-  if (!s_active) return;
 
   // ---- barriers and tensor memory
   if (threadIdx.x == 0) {
@@ -171,23 +167,27 @@ k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUten
   if (warp == 0) {
     // ---- TMA producer
     if (lane == 0) {
-      for (int kb = 0; kb < nkb; ++kb) {
+      // phases: a^T r (nphase 1); a1^T r1, a1^T r2, a2^T r1 (nphase 3)
+      const int nk = nkb * nphase;
+      for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % TC_STAGES;
         const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+        const int phase = kb / nkb, kk = kb - phase * nkb;
         if (kb >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
           s_fail = 1;
           break;
         }
         mbar_expect_tx(&full[s], (uint32_t)(TC_BM + TC_BN) * 128u);
-        tma_load_2d(&tma, &full[s], sA + s * TC_BM * 128, kb * KB_ELEMS, (int)m0);
-        tma_load_2d(&tmb, &full[s], sB + s * TC_BN * 128, kb * KB_ELEMS, (int)n0);
+        tma_load_2d(phase == 2 ? &tma2 : &tma, &full[s], sA + s * TC_BM * 128, kk * KB_ELEMS, (int)m0);
+        tma_load_2d(phase == 1 ? &tmb2 : &tmb, &full[s], sB + s * TC_BN * 128, kk * KB_ELEMS, (int)n0);
       }
     }
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = umma_idesc(FP8 ? 0u : 1u, TC_BM, TC_BN);
-      for (int kb = 0; kb < nkb; ++kb) {
+      const int nk = nkb * nphase;
+      for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % TC_STAGES;
         const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
         if (!mbar_wait(&full[s], ph)) {
@@ -218,8 +218,7 @@ k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUten
       if (ok && row < K) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const int64_t b = n0 + c0 + i;
-          if (s_on[c0 + i]) Gfull[b * K + row] = __uint_as_float(r[i]) * sc * s_sigma[c0 + i];
+          if (s_on[c0 + i]) Gfull[(int64_t)s_sig[c0 + i] * K + row] = __uint_as_float(r[i]) * sc * s_sigma[c0 + i];
         }
       }
     }
@@ -268,19 +267,32 @@ static int encode_2d(CUtensorMap* map, const void* ptr, int64_t rows, int64_t ld
   return LASSO_OK;
 }
 
-int tc_make_operands(const void* level_data, int64_t K, const void* rq, int64_t B, int64_t ldN, int fp8,
-                     TcOperands* out) {
+int tc_make_operands(const void* level_data, const void* level_data2, int64_t K, const void* rq, const void* rq2,
+                     int64_t B, int64_t ldN, int fp8, TcOperands* out) {
+  const bool split = level_data2 != nullptr || rq2 != nullptr;
   if ((ldN * (fp8 ? 1 : 2)) % 16 != 0 || (reinterpret_cast<uintptr_t>(level_data) & 15) ||
-      (reinterpret_cast<uintptr_t>(rq) & 15))
+      (reinterpret_cast<uintptr_t>(rq) & 15) || (split && (fp8 || !level_data2 || !rq2)) ||
+      (reinterpret_cast<uintptr_t>(level_data2) & 15) || (reinterpret_cast<uintptr_t>(rq2) & 15))
     return LASSO_ERR_INVALID_ARG;
   out->fp8 = fp8;
+  out->nphase = split ? 3 : 1;
   int rc = encode_2d(&out->a, level_data, K, ldN, fp8, TC_BM);
   if (rc) return rc;
-  return encode_2d(&out->b, rq, B, ldN, fp8, TC_BN);
+  rc = encode_2d(&out->b, rq, B, ldN, fp8, TC_BN);
+  if (rc) return rc;
+  if (!split) {
+    out->a2 = out->a;
+    out->b2 = out->b;
+    return LASSO_OK;
+  }
+  rc = encode_2d(&out->a2, level_data2, K, ldN, 0, TC_BM);
+  if (rc) return rc;
+  return encode_2d(&out->b2, rq2, B, ldN, 0, TC_BN);
 }
 
 void tc_launch_corr(const TcOperands& ops, int64_t K, int64_t B, int64_t ldN, const float* scale,
-                    const float* sigma, const SigState* st, int lvl, float* Gfull, int* err, cudaStream_t stream) {
+                    const float* sigma, const int* list, const int* count, float* Gfull, int* err,
+                    cudaStream_t stream) {
   static bool attr[2] = {false, false};
   const int es = ops.fp8 ? 1 : 2;
   const int nkb = (int)((ldN * es + 127) / 128);   // 128-byte K-slices (TMA zero-fills the tail)
@@ -290,13 +302,15 @@ void tc_launch_corr(const TcOperands& ops, int64_t K, int64_t B, int64_t ldN, co
       cudaFuncSetAttribute(k_tc_corr<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
       attr[1] = true;
     }
-    k_tc_corr<1><<<grid, TC_THREADS, TC_SMEM, stream>>>(ops.a, ops.b, K, B, nkb, scale, sigma, st, lvl, Gfull, err);
+    k_tc_corr<1><<<grid, TC_THREADS, TC_SMEM, stream>>>(ops.a, ops.b, ops.a2, ops.b2, K, B, nkb, ops.nphase, scale,
+                                                        sigma, list, count, Gfull, err);
   } else {
     if (!attr[0]) {
       cudaFuncSetAttribute(k_tc_corr<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
       attr[0] = true;
     }
-    k_tc_corr<0><<<grid, TC_THREADS, TC_SMEM, stream>>>(ops.a, ops.b, K, B, nkb, scale, sigma, st, lvl, Gfull, err);
+    k_tc_corr<0><<<grid, TC_THREADS, TC_SMEM, stream>>>(ops.a, ops.b, ops.a2, ops.b2, K, B, nkb, ops.nphase, scale,
+                                                        sigma, list, count, Gfull, err);
   }
 }
 
@@ -340,16 +354,24 @@ __device__ __forceinline__ double tc_val(const uint8_t* p, int64_t idx, int fp8)
 }
 
 // FP64 reference and error statistics: err / sum|a r| and err / (gamma_n(u_tc) sum|a r|).
-__global__ void k_tc_check(const uint8_t* __restrict__ A, const uint8_t* __restrict__ R, const float* __restrict__ G,
-                           int64_t K, int64_t B, int64_t ld, int fp8, double gam, unsigned long long* __restrict__ out) {
+// Split mode (A2, R2 non-null): the reference is a1^T r1 + a1^T r2 + a2^T r1.
+__global__ void k_tc_check(const uint8_t* __restrict__ A, const uint8_t* __restrict__ R, const uint8_t* __restrict__ A2,
+                           const uint8_t* __restrict__ R2, const float* __restrict__ G, int64_t K, int64_t B, int64_t ld,
+                           int fp8, double gam, unsigned long long* __restrict__ out) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= K * B) return;
   const int64_t j = t % K, b = t / K;
   double s = 0.0, sa = 0.0;
   for (int64_t n = 0; n < ld; ++n) {
-    const double p = tc_val(A, j * ld + n, fp8) * tc_val(R, b * ld + n, fp8);
+    const double a = tc_val(A, j * ld + n, fp8), r = tc_val(R, b * ld + n, fp8);
+    const double p = a * r;
     s += p;
     sa += fabs(p);
+    if (A2) {
+      const double p2 = a * tc_val(R2, b * ld + n, 0), p3 = tc_val(A2, j * ld + n, 0) * r;
+      s += p2 + p3;
+      sa += fabs(p2) + fabs(p3);
+    }
   }
   const double err = fabs((double)G[b * K + j] - s);
   const double rel = sa > 0.0 ? err / sa : 0.0;
@@ -358,34 +380,39 @@ __global__ void k_tc_check(const uint8_t* __restrict__ A, const uint8_t* __restr
   atomicMax(&out[1], __double_as_longlong(ratio));
 }
 
-int tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel, double* max_ratio) {
+int tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel, double* max_ratio) {
+  const int fp8 = mode == 1 ? 1 : 0;
+  const bool split = mode == 2;
   const int64_t ld = round_up(N, 16);
   const int es = fp8 ? 1 : 2;
-  uint8_t *A = nullptr, *R = nullptr;
+  uint8_t *A = nullptr, *R = nullptr, *A2 = nullptr, *R2 = nullptr;
   float* G = nullptr;
-  SigState* st = nullptr;
   int* err = nullptr;
   unsigned long long* out = nullptr;
   int rc = LASSO_OK;
   if (cudaMalloc(&A, K * ld * es) != cudaSuccess || cudaMalloc(&R, B * ld * es) != cudaSuccess ||
-      cudaMalloc(&G, K * B * 4) != cudaSuccess || cudaMalloc(&st, B * sizeof(SigState)) != cudaSuccess ||
-      cudaMalloc(&err, 4) != cudaSuccess || cudaMalloc(&out, 16) != cudaSuccess)
+      cudaMalloc(&G, K * B * 4) != cudaSuccess || cudaMalloc(&err, 4) != cudaSuccess ||
+      cudaMalloc(&out, 16) != cudaSuccess ||
+      (split && (cudaMalloc(&A2, K * ld * 2) != cudaSuccess || cudaMalloc(&R2, B * ld * 2) != cudaSuccess)))
     rc = LASSO_ERR_NOMEM;
   double rel = 0.0, ratio = 0.0;
   for (int positive = 0; positive < 2 && rc == LASSO_OK; ++positive) {
-    cudaMemset(st, 0, B * sizeof(SigState));   // every signal on level 0, not done
     cudaMemset(err, 0, 4);
     cudaMemset(out, 0, 16);
     cudaMemset(G, 0, K * B * 4);
     k_tc_fill<<<1024, 256>>>(A, K, ld, N, fp8, positive, 11 + positive);
     k_tc_fill<<<1024, 256>>>(R, B, ld, N, fp8, positive, 29 + positive);
+    if (split) {
+      k_tc_fill<<<1024, 256>>>(A2, K, ld, N, 0, positive, 47 + positive);
+      k_tc_fill<<<1024, 256>>>(R2, B, ld, N, 0, positive, 53 + positive);
+    }
     TcOperands ops;
-    rc = tc_make_operands(A, K, R, B, ld, fp8, &ops);
+    rc = tc_make_operands(A, A2, K, R, R2, B, ld, fp8, &ops);
     if (rc) break;
-    tc_launch_corr(ops, K, B, ld, nullptr, nullptr, st, 0, G, err, 0);
+    tc_launch_corr(ops, K, B, ld, nullptr, nullptr, nullptr, nullptr, G, err, 0);
     const int nk = (int)(ld / (fp8 ? 32 : 16));
-    const double gam = gamma_n((double)ld + nk, fp8 ? TC_U_FP8 : TC_U_BF16);
-    k_tc_check<<<(unsigned)((K * B + 255) / 256), 256>>>(A, R, G, K, B, ld, fp8, gam, out);
+    const double gam = gamma_n(((double)ld + nk) * (split ? 3.0 : 1.0), fp8 ? TC_U_FP8 : TC_U_BF16);
+    k_tc_check<<<(unsigned)((K * B + 255) / 256), 256>>>(A, R, A2, R2, G, K, B, ld, fp8, gam, out);
     int herr = 0;
     unsigned long long h[2] = {0, 0};
     if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -406,8 +433,9 @@ int tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel, doubl
   }
   cudaFree(A);
   cudaFree(R);
+  cudaFree(A2);
+  cudaFree(R2);
   cudaFree(G);
-  cudaFree(st);
   cudaFree(err);
   cudaFree(out);
   if (max_rel) *max_rel = rel;
@@ -417,8 +445,8 @@ int tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel, doubl
 
 }  // namespace lasso
 
-extern "C" int lasso_tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel_err,
+extern "C" int lasso_tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel_err,
                                  double* max_err_over_bound) {
-  if (K <= 0 || N <= 0 || B <= 0 || K * B > (int64_t)1 << 28) return LASSO_ERR_INVALID_ARG;
-  return lasso::tc_selftest(fp8 ? 1 : 0, K, N, B, max_rel_err, max_err_over_bound);
+  if (K <= 0 || N <= 0 || B <= 0 || K * B > (int64_t)1 << 28 || mode < 0 || mode > 2) return LASSO_ERR_INVALID_ARG;
+  return lasso::tc_selftest(mode, K, N, B, max_rel_err, max_err_over_bound);
 }

@@ -22,21 +22,28 @@ constexpr double TC_U_FP8 = 1.9073486328125e-06;      // 2^-19
 
 struct TcOperands {
   CUtensorMap a;          // dictionary level: K rows (atoms) x ldN, K-major
-  CUtensorMap b;          // quantised residuals: B rows (signals) x ldN, K-major
+  CUtensorMap b;          // quantised residuals: B rows (signal slots) x ldN, K-major
+  CUtensorMap a2, b2;     // split form (nphase 3): second BF16 parts of the atoms / residuals
   int fp8;                // 1: kind::f8f6f4 E4M3, 0: kind::f16 BF16
+  int nphase;             // 1: a^T r; 3: a1^T r1 + a1^T r2 + a2^T r1 in one accumulator
 };
 
-// Encode the two tensor maps (host).  Returns LASSO_OK or an error status.
-int tc_make_operands(const void* level_data, int64_t K, const void* rq, int64_t B, int64_t ldN, int fp8,
-                     TcOperands* out);
+// Encode the tensor maps (host); level_data2 / rq2 non-null selects the split form.  Returns
+// LASSO_OK or an error status.
+int tc_make_operands(const void* level_data, const void* level_data2, int64_t K, const void* rq, const void* rq2,
+                     int64_t B, int64_t ldN, int fp8, TcOperands* out);
 
-// Gfull[b][j] = scale_j * sigma_b * sum_n q_jn r^_bn for the signals b at ladder level `lvl`
-// (tiles with no such signal exit at once).  err: set to 1 if a pipeline wait gave up.
+// Gfull[b][j] = scale_j * sigma_b * sum_n q_jn r^_bn for the signals listed in slots
+// [0, *count) of `list` (row s of the residual operand belongs to signal list[s]); tiles past the
+// count exit at once.  list == nullptr: slot s is signal s (count B).  err: set to 1 if a
+// pipeline wait gave up.
 void tc_launch_corr(const TcOperands& ops, int64_t K, int64_t B, int64_t ldN, const float* scale,
-                    const float* sigma, const SigState* st, int lvl, float* Gfull, int* err, cudaStream_t stream);
+                    const float* sigma, const int* list, const int* count, float* Gfull, int* err,
+                    cudaStream_t stream);
 
 // Self-test: random K x N operands and B signals through the tensor-core GEMM, compared with an
 // FP64 evaluation of the same products; reports the largest error relative to sum |a_i r_i|.
-int tc_selftest(int fp8, int64_t K, int64_t N, int64_t B, double* max_rel, double* max_abs_bound_ratio);
+// mode 0: BF16, 1: E4M3, 2: split BF16 (three products in one accumulator).
+int tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel, double* max_abs_bound_ratio);
 
 }  // namespace lasso
