@@ -15,7 +15,7 @@ namespace lasso {
 constexpr int MAX_LEVELS = 8;
 constexpr int VEC_BYTES = 16;        // every dense row is padded to a multiple of 16 elements
 constexpr int CORR_CHUNK = 32;       // smallest work item (atoms of the preserved list); batches use 4x
-constexpr int RES_THREADS = 256;
+constexpr int RES_THREADS = 512;
 
 // Arithmetic kind of a level.
 enum LevelKind : int {
@@ -94,6 +94,11 @@ struct SigState {
   float thr_f, beta_f;               // lam / L and the FISTA momentum, as FP32 (update of the pass)
   float c_nrho_ru;                   // ||rho^|| of the snapshot, rounded up
   unsigned pm1, pm2;                 // per-pass maxima of the correlation (FP32 bit patterns, >= 0)
+  double e_m1, e_m2;                 // the pass's maxima as evaluated (kept for the refinement)
+  double e_wm;                       // refinement: max over the recomputed candidates (tight bounds)
+  // screening scalars of the pass: |s'|, |s'| ||rho||, test radius, |s~|, R~, 1 / lam
+  double t_abs_sp, t_c_eps, t_Rs, t_abs_st, t_Rt, t_inv_lam;
+  int act, scr, snap, refine;        // outcome of the pass, screen flag, snapshot, tighten request
   int c_nnz, pending, next_check, pad1;
   int level, n_kept, parity, n_nz, status, done, iters, Kt, n_chunks, pad0;
   int level_passes[MAX_LEVELS];

@@ -492,6 +492,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
         __syncthreads();
         const int cnt = min(RES_THREADS, nnz - base);
         if (active && L.kind == LK_F32) {
+#pragma unroll 4
           for (int q = 0; q < cnt; ++q) {
             const float4 av = load4_f(L, s_idx[q], r0);
             const float w = s_wf[q];
@@ -880,18 +881,228 @@ __global__ void k_init_finish(PassArgs<VT> a, int lambda_relative) {
 
 // ------------------------------------------------------------------ gap, screening, switch
 
-// One block per signal.  Thread 0 evaluates the FP64 scalars of the pass:
+// FP64 scalars of one pass of one signal, for an upper bound m1 of max_j (|a_j^T rho| +
+// eps_j ||rho||) and m2 = max_j |g^_j|:
 //   P = 1/2||rho||^2 + lam ||z||_1, theta' = s' rho (stable scaling), theta~ = s~ rho,
 //   G' = P - D(theta'), G~ = P - D(theta~), delta = ||rho|| e + e^2/2 with
-//   e = sum eps_j |z_j| + (residual rounding), R' = sqrt(2 G' + 2 delta) / lam,
-//   gamma = G~ / G', stop when the level is exact and (G' + delta) / ||y||^2 <= tol.
-// Then, in one sweep of the preserved list, every atom is tested (stable GAP or Dynamic Safe
+//   e = sum eps_j |z_j| + (residual rounding), R' = sqrt(2 G' + 2 delta) / lam, gamma = G~ / G',
+//   and the certificate (G' + delta) / ||y||^2 of the reduced problem.
+struct PassScalars {
+  double Gp, Gt, delta, Rp, gamma, sp, abs_st, Rt, cert;
+};
+
+template <typename VT>
+__device__ PassScalars pass_scalars(const SigState& s, const LevelDev& L, double rr, double yr, double m1, double m2) {
+  PassScalars o;
+  const double lam = s.lam;
+  const double nrho = sqrt(rr);
+  const double e_r = residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8);
+  const double e = s.sum_epsz + e_r;
+  double sp_ = 0.0, st_ = 0.0;
+  if (rr > 0.0) {
+    const double beta = yr / (lam * rr);
+    sp_ = m1 > 0.0 ? fmin(fmax(beta, -1.0 / m1), 1.0 / m1) : beta;
+    st_ = m2 > 0.0 ? fmin(fmax(beta, -1.0 / m2), 1.0 / m2) : beta;
+  }
+  const double P = 0.5 * rr + lam * s.l1;
+  const double Dp = lam * sp_ * yr - 0.5 * lam * lam * sp_ * sp_ * rr;
+  const double Dt = lam * st_ * yr - 0.5 * lam * lam * st_ * st_ * rr;
+  o.Gp = P - Dp;
+  o.Gt = P - Dt;
+  o.delta = nrho * e + 0.5 * e * e;
+  o.Rp = sqrt(fmax(2.0 * o.Gp + 2.0 * o.delta, 0.0)) / lam;
+  o.gamma = o.Gp > 0.0 ? o.Gt / o.Gp : 0.0;
+  o.sp = sp_;
+  o.abs_st = fabs(st_);
+  o.Rt = sqrt(fmax(2.0 * o.Gt, 0.0)) / lam;
+  o.cert = fmax(o.Gp + o.delta, 0.0) / s.yy;
+  return o;
+}
+
+__device__ __forceinline__ void apply_scalars(SigState& s, const PassScalars& ps) {
+  s.Gp = ps.Gp;
+  s.Gt = ps.Gt;
+  s.delta = ps.delta;
+  s.Rp = ps.Rp;
+  s.gamma = ps.gamma;
+  s.sp = ps.sp;
+}
+
+// Outcome of the pass for one signal once its certificate is known: stop (converged, or an
+// error), snapshot the point for the full-dictionary check, or continue; and the scalars of the
+// screening test.  m1_bulk: the pass's own maximum (finiteness check); m1_used: the one the
+// certificate used (tightened by the refinement).
+template <typename VT>
+__device__ void pass_decide(SigState& s, const PassArgs<VT>& a, double m1_bulk, double m1_used,
+                            const PassScalars& ps) {
+  const int I = a.dd.n_levels - 1;
+  const double rr = s.rr, yr = s.yr, gcert = ps.cert;
+  const double lam = s.lam;
+  const double nrho = sqrt(rr);
+  int action = 0;   // 0 continue, 1 stop (converged), 2 stop (error)
+  s.snap = 0;       // 1: snapshot the point for the full-dictionary check
+  if (!(rr < INFINITY) || !(yr == yr) || !(m1_bulk < INFINITY) || !(s.Gp == s.Gp) || !(s.delta < INFINITY)) {
+    s.status = LASSO_ERR_NONFINITE;
+    action = 2;
+  } else if (s.level == I && gcert <= a.sp.tol && !a.sp.full_gap) {
+    s.status = LASSO_OK;
+    action = 1;
+  } else if (s.level == I && gcert <= a.sp.tol && !s.pending && s.iters >= s.next_check) {
+    // the reduced problem is solved to tol: keep iterating while this point's correlations
+    // with the rejected atoms are checked (full-dictionary gap, stopping rule of Section IV)
+    s.pending = 1;
+    s.snap = 1;
+  } else if (s.iters >= a.sp.max_iter) {
+    s.status = LASSO_ERR_MAXITER;
+    action = 2;
+  }
+  if (s.level == I || action) s.gap = gcert;
+  if (action || s.snap) {
+    // the scalars of the point that is returned or checked (full-dictionary gap, audit)
+    s.c_rr = rr;
+    s.c_yr = yr;
+    s.c_l1 = s.l1;
+    s.c_epsz = s.sum_epsz;
+    s.c_kapz = s.sum_kapz;
+    s.c_nnz = s.n_nz;
+    s.c_m1 = m1_used;
+    s.c_nrho_ru = __double2float_ru(nrho);
+  }
+  // Dynamic Safe radius ||theta' - y/lam|| (Table I)
+  const double sp_ = s.sp;
+  const double inv_lam = 1.0 / lam;
+  const double d2 = sp_ * sp_ * rr - 2.0 * sp_ * yr * inv_lam + s.yy * inv_lam * inv_lam;
+  s.scr = rr > 0.0 && (s.iters % a.sp.screen_every) == 0 ? 1 : 0;
+  s.act = action;
+  s.t_abs_sp = fabs(sp_);
+  s.t_c_eps = fabs(sp_) * nrho;
+  s.t_Rs = a.sp.rule == LASSO_RULE_GAP ? s.Rp : sqrt(fmax(d2, 0.0)) * (1.0 + 4.0 * U64);
+  s.t_abs_st = ps.abs_st;
+  s.t_Rt = ps.Rt;
+  s.t_inv_lam = inv_lam * (1.0 + 2.0 * U64);
+}
+
+// FP64 scalars of the pass, one thread per signal (FP64 issue is shared by the 32 signals of a
+// warp instead of one): the certificate, the pass count, and either the outcome of the pass or,
+// on the exact FP32 level near convergence, the request to tighten the certificate (k_screen).
+template <typename VT, int FINISH>
+__global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.sp.B) return;
+  SigState* sp = a.st + b;
+  if (sp->done) return;
+  if (FINISH) {
+    // the certificate with the recomputed candidates (k_refine): max(max |g^|, tight bounds),
+    // never above the bulk bound
+    if (!sp->refine) return;
+    SigState s = *sp;
+    const LevelDev& L = a.dd.lv[s.level];
+    const double m1 = fmin(fmax(s.e_m2, s.e_wm), s.e_m1);
+    const PassScalars ps = pass_scalars<VT>(s, L, s.rr, s.yr, m1, s.e_m2);
+    apply_scalars(s, ps);
+    pass_decide<VT>(s, a, s.e_m1, m1, ps);
+    s.refine = 0;
+    *sp = s;
+    return;
+  }
+  SigState s = *sp;
+  const LevelDev& L = a.dd.lv[s.level];
+  const int I = a.dd.n_levels - 1;
+  const double rr = s.rr, yr = s.yr;
+  double m1 = 0.0, m2 = 0.0;
+  if constexpr (sizeof(VT) == 4) {
+    m1 = (double)__uint_as_float(s.pm1);
+    m2 = (double)__uint_as_float(s.pm2);
+    s.pm1 = 0u;
+    s.pm2 = 0u;
+  } else {
+    for (int c = 0; c < s.n_chunks; ++c) {
+      m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
+      m2 = fmax(m2, a.part_corr[((int64_t)b * a.nch + c) * 2 + 1]);
+    }
+  }
+  const PassScalars ps = pass_scalars<VT>(s, L, rr, yr, m1, m2);
+  apply_scalars(s, ps);
+  s.iters += 1;
+  s.level_passes[s.level] += 1;
+  if (a.alg_bytes) atomicAdd(&a.alg_bytes[8 + s.level], (double)s.n_kept);
+  s.e_m1 = m1;
+  s.e_m2 = m2;
+  s.refine = 0;
+  if (sizeof(VT) == 4 && L.kind == LK_F32 && s.level == I && ps.cert > a.sp.tol && rr > 0.0 && m2 > 0.0) {
+    // would the certificate meet tol with the tight products?  then k_screen tightens it
+    const PassScalars pe = pass_scalars<VT>(s, L, rr, yr, m2 * (1.0 + 3.0 * U32), m2);
+    if (pe.cert <= a.sp.tol) s.refine = 1;
+  }
+  if (!s.refine) pass_decide<VT>(s, a, m1, m1, ps);
+  *sp = s;
+}
+
+// Tightening of the certificate on the exact FP32 level (requested by k_eval when the gap
+// without the bulk pass's rounding margins already meets tol): the atoms that can attain the
+// maximum -- those whose loose upper bound exceeds max_j |g^_j|, every other atom being below
+// that maximum -- are recomputed from the FP32 data with error-free products.  One block per
+// signal; the lanes test 32 positions at once, the warp recomputes each candidate.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_refine(PassArgs<VT> a) {
+  const int b = blockIdx.x;
+  SigState* sp = a.st + b;
+  __shared__ int s_go;
+  __shared__ double s_wmax[8];
+  if (threadIdx.x == 0) s_go = !sp->done && sp->refine;
+  __syncthreads();
+  if (!s_go) return;
+  if constexpr (sizeof(VT) == 4) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const SigState& s = *sp;
+    const LevelDev& L = a.dd.lv[s.level];
+    const int n_kept = s.n_kept;
+    const int32_t* kp = kept_of(a, b, s.parity);
+    const VT* G = a.G + (int64_t)b * a.K;
+    const double T = s.e_m2, nrho = sqrt(s.rr);
+    const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
+    const float T_f = __double2float_rd(T);
+    // |g^_j - a_j^T rho| <= epsr_j ||rho|| (+ kappa_j dq for a quantised operand) + 3 u |g^_j|
+    const float nr_f = __double2float_ru(nrho);
+    const float dq_f = L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
+    double wm = 0.0;
+    for (int base = wid * 32; base < n_kept; base += 256) {
+      const int pos = base + lane;
+      int32_t j = 0;
+      bool cand = false;
+      if (pos < n_kept) {
+        j = kp[pos];
+        float ub = __fmaf_ru(L.epsr32[j], nr_f, __fmul_ru(fabsf((float)G[pos]), 1.0000004f));
+        if (dq_f > 0.f) ub = __fmaf_ru(L.kappa32[j], dq_f, ub);
+        cand = ub > T_f;
+      }
+      unsigned m = __ballot_sync(0xffffffffu, cand);
+      while (m) {
+        const int l = __ffs(m) - 1;
+        m &= m - 1;
+        const int64_t jj = __shfl_sync(0xffffffffu, j, l);
+        const double g = warp_atom_dot(L, jj, (int)a.ldN, rho, nullptr, lane);
+        wm = fmax(wm, fabs(g) * (1.0 + 3.0 * U32) + L.gam_tight * L.kappa[jj] * nrho);
+      }
+    }
+    if (lane == 0) s_wmax[wid] = wm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int w = 0; w < 8; ++w) m = fmax(m, s_wmax[w]);
+      sp->e_wm = m;
+    }
+  }
+}
+
+// One block per signal, after the pass has been evaluated (k_eval, and k_refine for a tightened
+// certificate).  In one sweep of the preserved list, every atom is tested (stable GAP or Dynamic Safe
 // sphere), K_t is counted, and the preserved list and the nonzero list of z+ are compacted in
 // order; Algorithm 2 picks the next level and the sums of the nonzero list close the pass.
 // FP32 iterates keep the per-atom work in FP32: tests rounded upward (over-estimating only
 // keeps atoms), sum |z_j| compensated, sum eps_j |z_j| and sum kappa_j |z_j| rounded upward.
 template <typename VT>
-__global__ void __launch_bounds__(SCREEN_THREADS, 3) k_screen(PassArgs<VT> a) {
+__global__ void __launch_bounds__(SCREEN_THREADS, 4) k_screen(PassArgs<VT> a) {
   constexpr bool F32 = sizeof(VT) == 4;
   constexpr int NWS = SCREEN_THREADS / 32;
   const int b = blockIdx.x;
@@ -902,186 +1113,33 @@ __global__ void __launch_bounds__(SCREEN_THREADS, 3) k_screen(PassArgs<VT> a) {
   __shared__ int s_cnt[2][SU][NWS];
   __shared__ int s_warp3[NWS];
   __shared__ double s_red[3][NWS];
-  __shared__ double s_wmax[NWS];
-  if (threadIdx.x == 0) si[11] = sp->done;
-  __syncthreads();
-  if (si[11]) return;
-  const int I = a.dd.n_levels - 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // FP64 scalars of the pass for a given upper bound m1 of max_j (|a_j^T rho| + eps_j ||rho||)
-  auto evaluate = [&](SigState& s, const LevelDev& L, double rr, double yr, double m1, double m2) {
-    const double lam = s.lam;
-    const double nrho = sqrt(rr);
-    const double e_r = residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8);
-    const double e = s.sum_epsz + e_r;
-    double sp_ = 0.0, st_ = 0.0;
-    if (rr > 0.0) {
-      const double beta = yr / (lam * rr);
-      sp_ = m1 > 0.0 ? fmin(fmax(beta, -1.0 / m1), 1.0 / m1) : beta;
-      st_ = m2 > 0.0 ? fmin(fmax(beta, -1.0 / m2), 1.0 / m2) : beta;
-    }
-    const double P = 0.5 * rr + lam * s.l1;
-    const double Dp = lam * sp_ * yr - 0.5 * lam * lam * sp_ * sp_ * rr;
-    const double Dt = lam * st_ * yr - 0.5 * lam * lam * st_ * st_ * rr;
-    s.Gp = P - Dp;
-    s.Gt = P - Dt;
-    s.delta = nrho * e + 0.5 * e * e;
-    s.Rp = sqrt(fmax(2.0 * s.Gp + 2.0 * s.delta, 0.0)) / lam;
-    s.gamma = s.Gp > 0.0 ? s.Gt / s.Gp : 0.0;
-    s.sp = sp_;
-    sc[3] = fabs(st_);
-    sc[4] = sqrt(fmax(2.0 * s.Gt, 0.0)) / lam;
-    return fmax(s.Gp + s.delta, 0.0) / s.yy;   // certificate of the reduced problem (relative)
-  };
   if (threadIdx.x == 0) {
-    SigState s = *sp;
-    const LevelDev& L = a.dd.lv[s.level];
-    const double rr = s.rr, yr = s.yr;
-    double m1 = 0.0, m2 = 0.0;
-    if constexpr (F32) {
-      m1 = (double)__uint_as_float(s.pm1);
-      m2 = (double)__uint_as_float(s.pm2);
-      s.pm1 = 0u;
-      s.pm2 = 0u;
-    } else {
-      for (int c = 0; c < s.n_chunks; ++c) {
-        m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
-        m2 = fmax(m2, a.part_corr[((int64_t)b * a.nch + c) * 2 + 1]);
-      }
-    }
-    const double gcert = evaluate(s, L, rr, yr, m1, m2);
-    s.iters += 1;
-    s.level_passes[s.level] += 1;
-    if (a.alg_bytes) atomicAdd(&a.alg_bytes[8 + s.level], (double)s.n_kept);
-    // The exact FP32 level bounds its bulk correlations loosely; when the gap without those
-    // margins already meets tol, the atoms that can attain the maximum are recomputed with
-    // error-free products (below) to tighten the certificate.
-    int refine = 0;
-    if (F32 && L.kind == LK_F32 && s.level == I && gcert > a.sp.tol && rr > 0.0 && m2 > 0.0) {
-      SigState t = s;
-      const double mest = m2 * (1.0 + 3.0 * U32);
-      if (evaluate(t, L, rr, yr, mest, m2) <= a.sp.tol) refine = 1;
-    }
-    sc[8] = rr;
-    sc[9] = yr;
-    sc[10] = m1;
-    sc[11] = m2;
-    sc[12] = gcert;
-    sc[13] = m1;
-    si[1] = refine;
+    const SigState& s = *sp;
+    si[11] = s.done;
     si[4] = s.n_kept;
     si[5] = s.parity;
     si[6] = s.level;
     si[7] = s.n_nz;
-    *sp = s;
+    sc[0] = s.t_abs_sp;
+    sc[1] = s.t_c_eps;
+    sc[2] = s.t_Rs;
+    sc[3] = s.t_abs_st;
+    sc[4] = s.t_Rt;
+    sc[5] = 1.0 - a.sp.tau;
+    sc[6] = 1.0 + 3.0 * (level_fp64_arith(a.dd.lv[s.level].kind) && sizeof(VT) == 8 ? U64 : U32);
+    sc[7] = s.t_inv_lam;
+    sc[14] = s.dq;
+    si[0] = s.act;
+    si[1] = s.scr;
+    si[2] = s.snap;
   }
   __syncthreads();
+  if (si[11]) return;
   const int n_kept = si[4], parity = si[5], level = si[6], n_nz = si[7];
   const LevelDev& L = a.dd.lv[level];
   const int32_t* kp = kept_of(a, b, parity);
   const VT* G = a.G + (int64_t)b * a.K;
-  if constexpr (F32) {
-    if (si[1]) {
-      // candidates: atoms whose loose upper bound exceeds max_j |g^_j| (every other atom is
-      // below that maximum); the lanes test 32 positions at once, the warp recomputes each
-      // candidate with error-free products
-      const double T = sc[11], nrho = sqrt(sc[8]);
-      const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
-      const float T_f = __double2float_rd(T);
-      // |g^_j - a_j^T rho| <= epsr_j ||rho|| (+ kappa_j dq for a quantised operand) + 3 u |g^_j|
-      const float nr_f = __double2float_ru(nrho);
-      const float dq_f = L.tc ? __double2float_ru(sp->dq * 1.001) : 0.f;
-      double wm = 0.0;
-      for (int base = wid * 32; base < n_kept; base += SCREEN_THREADS) {
-        const int pos = base + lane;
-        int32_t j = 0;
-        bool cand = false;
-        if (pos < n_kept) {
-          j = kp[pos];
-          float ub = __fmaf_ru(L.epsr32[j], nr_f, __fmul_ru(fabsf((float)G[pos]), 1.0000004f));
-          if (dq_f > 0.f) ub = __fmaf_ru(L.kappa32[j], dq_f, ub);
-          cand = ub > T_f;
-        }
-        unsigned m = __ballot_sync(0xffffffffu, cand);
-        while (m) {
-          const int l = __ffs(m) - 1;
-          m &= m - 1;
-          const int64_t jj = __shfl_sync(0xffffffffu, j, l);
-          const double g = warp_atom_dot(L, jj, (int)a.ldN, rho, nullptr, lane);
-          wm = fmax(wm, fabs(g) * (1.0 + 3.0 * U32) + L.gam_tight * L.kappa[jj] * nrho);
-        }
-      }
-      if (lane == 0) s_wmax[wid] = wm;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double m1 = T;
-        for (int w = 0; w < NWS; ++w) m1 = fmax(m1, s_wmax[w]);
-        SigState s2 = *sp;
-        sc[13] = fmin(m1, sc[10]);
-        sc[12] = evaluate(s2, L, sc[8], sc[9], sc[13], sc[11]);
-        *sp = s2;
-      }
-      __syncthreads();
-    }
-  }
-  if (threadIdx.x == 0) {
-    SigState s = *sp;
-    const double rr = sc[8], yr = sc[9], gcert = sc[12];
-    const double lam = s.lam;
-    const double nrho = sqrt(rr);
-    int action = 0;   // 0 continue, 1 stop (converged), 2 stop (error)
-    si[2] = 0;        // 1: snapshot the point for the full-dictionary check
-    if (!(rr < INFINITY) || !(yr == yr) || !(sc[10] < INFINITY) || !(s.Gp == s.Gp) || !(s.delta < INFINITY)) {
-      s.status = LASSO_ERR_NONFINITE;
-      action = 2;
-    } else if (s.level == I && gcert <= a.sp.tol && !a.sp.full_gap) {
-      s.status = LASSO_OK;
-      action = 1;
-    } else if (s.level == I && gcert <= a.sp.tol && !s.pending && s.iters >= s.next_check) {
-      // the reduced problem is solved to tol: keep iterating while this point's correlations
-      // with the rejected atoms are checked (full-dictionary gap, stopping rule of Section IV)
-      s.pending = 1;
-      s.c_rr = rr;
-      s.c_yr = yr;
-      s.c_l1 = s.l1;
-      s.c_epsz = s.sum_epsz;
-      s.c_kapz = s.sum_kapz;
-      s.c_nnz = s.n_nz;
-      s.c_m1 = sc[13];
-      s.c_nrho_ru = __double2float_ru(nrho);
-      si[2] = 1;
-    } else if (s.iters >= a.sp.max_iter) {
-      s.status = LASSO_ERR_MAXITER;
-      action = 2;
-    }
-    if (s.level == I || action) s.gap = gcert;
-    if (action) {
-      // the returned point's scalars (used by the optional full-dictionary audit)
-      s.c_rr = rr;
-      s.c_yr = yr;
-      s.c_l1 = s.l1;
-      s.c_epsz = s.sum_epsz;
-      s.c_kapz = s.sum_kapz;
-      s.c_nnz = s.n_nz;
-      s.c_m1 = sc[13];
-      s.c_nrho_ru = __double2float_ru(nrho);
-    }
-    // Dynamic Safe radius ||theta' - y/lam|| (Table I)
-    const double sp_ = s.sp;
-    const double d2 = sp_ * sp_ * rr - 2.0 * sp_ * yr / lam + s.yy / (lam * lam);
-    const bool screen = rr > 0.0 && (s.iters % a.sp.screen_every) == 0;
-    sc[0] = fabs(sp_);
-    sc[1] = fabs(sp_) * nrho;
-    sc[2] = a.sp.rule == LASSO_RULE_GAP ? s.Rp : sqrt(fmax(d2, 0.0));
-    sc[5] = 1.0 - a.sp.tau;
-    sc[6] = 1.0 + 3.0 * (level_fp64_arith(a.dd.lv[s.level].kind) && sizeof(VT) == 8 ? U64 : U32);
-    sc[7] = 1.0 / lam;
-    sc[14] = s.dq;
-    si[0] = action;
-    si[1] = screen ? 1 : 0;
-    *sp = s;
-  }
-  __syncthreads();
   const int action = si[0];
   VT* X = a.X + (int64_t)b * a.K;
   VT* Z = a.Z + (int64_t)b * a.K;
@@ -1235,6 +1293,7 @@ __global__ void __launch_bounds__(SCREEN_THREADS, 3) k_screen(PassArgs<VT> a) {
     int t = 0;
     for (int w = 0; w < NWS; ++w) t += s_warp3[w];
     // Algorithm 2
+    const int I = a.dd.n_levels - 1;
     int nl = level;
     if (level < I) {
       if (t <= L.rc * (double)a.K) nl = I;
@@ -1847,6 +1906,11 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   if constexpr (sizeof(VT) == 4) k_corr_pass<VT><<<corr_grid, CORR_THREADS, 0, st>>>(pa);
   else k_corr<VT, CORR_PASS><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
+  k_eval<VT, 0><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa);
+  if constexpr (sizeof(VT) == 4) {
+    k_refine<VT><<<B, 256, 0, st>>>(pa);
+    k_eval<VT, 1><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa);
+  }
   k_screen<VT><<<B, SCREEN_THREADS, 0, st>>>(pa);
   if (pa.sp.full_gap) {
     k_schedule_full<VT><<<1, 1024, 0, st>>>(pa);
@@ -1859,7 +1923,7 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
 }
 
 static int pass_launches(bool has_kron, bool full_gap, int n_tc) {
-  return (has_kron ? 9 : 4) + (full_gap ? 3 : 0) + 2 * n_tc;
+  return (has_kron ? 12 : 7) + (full_gap ? 3 : 0) + 2 * n_tc;
 }
 
 template <typename VT>
