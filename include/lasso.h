@@ -138,6 +138,12 @@ typedef struct {
                                 the deciding atoms from the FP32 data.  Default 0: the tensor
                                 cores' FP32 accumulation is too coarse for the last decades of
                                 the gap (FISTA needs more passes, some signals stall near 1e-6) */
+    int fp64_fallback;       /* 1 (default): a signal whose certificate stops improving on the exact
+                                FP32 level (FP32 iterates at their precision floor, e.g. on very
+                                coherent dictionaries) is stopped and solved again from scratch
+                                with FP64 iterates and an FP64-accumulation rung, as final_fp64
+                                does; its outputs replace the FP32 ones.  0: such a signal ends
+                                with LASSO_ERR_MAXITER.                                          */
 } lasso_opts;
 
 /* Fill *opts with the defaults above. */
@@ -159,6 +165,7 @@ typedef struct {
     double kernel_ms[6];
     double kernel_bytes[6];
     double level_atoms[8];   /* sum over passes and signals of |A_t| on each level              */
+    int64_t fp64_resolved;   /* signals solved again with FP64 iterates (opts.fp64_fallback)     */
 } lasso_stats;
 
 /* Solve one signal (host buffers).  y: N values (rounded to the exact level's precision on

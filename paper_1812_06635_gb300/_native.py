@@ -29,6 +29,7 @@ class LassoOpts(C.Structure):
         ("profile", C.c_int),
         ("full_gap", C.c_int),
         ("tc_exact", C.c_int),
+        ("fp64_fallback", C.c_int),
     ]
 
 
@@ -45,6 +46,7 @@ class LassoStats(C.Structure):
         ("kernel_ms", C.c_double * 6),
         ("kernel_bytes", C.c_double * 6),
         ("level_atoms", C.c_double * 8),
+        ("fp64_resolved", C.c_int64),
     ]
 
 

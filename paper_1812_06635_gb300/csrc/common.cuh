@@ -99,6 +99,8 @@ struct SigState {
   // screening scalars of the pass: |s'|, |s'| ||rho||, test radius, |s~|, R~, 1 / lam
   double t_abs_sp, t_c_eps, t_Rs, t_abs_st, t_Rt, t_inv_lam;
   int act, scr, snap, refine;        // outcome of the pass, screen flag, snapshot, tighten request
+  double best_cert;                  // exact level: best certificate so far
+  int stall, pad2;                   // exact level: passes without a 2 % improvement of it
   int c_nnz, pending, next_check, pad1;
   int level, n_kept, parity, n_nz, status, done, iters, Kt, n_chunks, pad0;
   int level_passes[MAX_LEVELS];
@@ -116,7 +118,13 @@ struct SolveParams {
   int B;
   int chunk;                // atoms per correlation work item (multiple of CORR_CHUNK)
   int full_gap;             // 1: stop on the full-dictionary gap (checked explicitly)
+  int stall_passes;         // exact FP32 level: passes without progress that mark a signal saturated (0: off)
 };
+
+// Internal status of a signal whose FP32 iterates stopped improving on the exact level: the
+// host solves it again with FP64 iterates (never returned to callers; reported as
+// LASSO_ERR_MAXITER when that second solve is disabled).
+constexpr int LASSO_ST_SATURATED = 2;
 
 // ------------------------------------------------------------------ error-free transforms
 // TwoSum (Knuth): s + e == a + b exactly.

@@ -1035,6 +1035,7 @@ void lasso_workspace_free(lasso::Workspace* ws);
 extern "C" void lasso_dict_destroy(lasso_dict* d) {
   if (!d) return;
   if (d->ws) lasso_workspace_free(d->ws);
+  if (d->ws64) lasso_workspace_free(d->ws64);
   for (auto& h : d->approx) free_level(h);
   cudaFree(d->exact.dscale);
   d->exact.dscale = nullptr;

@@ -55,7 +55,8 @@ struct lasso_dict {
   lasso::HostLevel rung64;             // FP64-accumulation rung on FP32 exact data (lazy)
   double L = 0.0;
   bool prepared = false;
-  lasso::Workspace* ws = nullptr;
+  lasso::Workspace* ws = nullptr;     // FP32-iterate solves
+  lasso::Workspace* ws64 = nullptr;   // FP64-iterate solves
 };
 
 namespace lasso {

@@ -95,13 +95,14 @@ static int ws_alloc(void** p, size_t bytes) {
 }
 
 static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
-  Workspace* w = d->ws;
-  if (w && w->B >= B && w->vt_double == vt_double) {
+  Workspace*& slot = vt_double ? d->ws64 : d->ws;
+  Workspace* w = slot;
+  if (w && w->B >= B) {
     *out = w;
     return LASSO_OK;
   }
   if (w) free_ws(w);
-  d->ws = nullptr;
+  slot = nullptr;
   w = new Workspace();
   w->B = B;
   w->K = d->K;
@@ -155,7 +156,7 @@ static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
     free_ws(w);
     return LASSO_ERR_NOMEM;
   }
-  d->ws = w;
+  slot = w;
   *out = w;
   return LASSO_OK;
 }
@@ -281,6 +282,7 @@ __global__ void k_init_state(PassArgs<VT> a, const double* __restrict__ lambdas)
     st.n_kept = (int)a.K;
     st.n_chunks = (int)((a.K + a.sp.chunk - 1) / a.sp.chunk);
     st.gap = INFINITY;
+    st.best_cert = INFINITY;
     st.status = LASSO_OK;
     if (!(yy < INFINITY) || !(st.lam == st.lam)) {
       st.status = LASSO_ERR_NONFINITE;
@@ -982,6 +984,21 @@ __device__ void pass_decide(SigState& s, const PassArgs<VT>& a, double m1_bulk, 
   s.t_inv_lam = inv_lam * (1.0 + 2.0 * U64);
 }
 
+// Saturation of the FP32 iterates on the exact level: the certificate has not improved by 2 %
+// for stall_passes passes while still above tol; the signal stops and is solved again with
+// FP64 iterates by the host.
+template <typename VT>
+__device__ __forceinline__ void check_stall(SigState& s, const PassArgs<VT>& a, double cert) {
+  if (a.sp.stall_passes <= 0 || s.level != a.dd.n_levels - 1 || s.act != 0 || s.pending) return;
+  if (cert < 0.98 * s.best_cert) {
+    s.best_cert = cert;
+    s.stall = 0;
+  } else if (++s.stall >= a.sp.stall_passes && cert > a.sp.tol) {
+    s.status = LASSO_ST_SATURATED;
+    s.act = 2;
+  }
+}
+
 // FP64 scalars of the pass, one thread per signal (FP64 issue is shared by the 32 signals of a
 // warp instead of one): the certificate, the pass count, and either the outcome of the pass or,
 // on the exact FP32 level near convergence, the request to tighten the certificate (k_screen).
@@ -1001,6 +1018,7 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
     const PassScalars ps = pass_scalars<VT>(s, L, s.rr, s.yr, m1, s.e_m2);
     apply_scalars(s, ps);
     pass_decide<VT>(s, a, s.e_m1, m1, ps);
+    check_stall<VT>(s, a, ps.cert);
     s.refine = 0;
     *sp = s;
     return;
@@ -1034,7 +1052,10 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
     const PassScalars pe = pass_scalars<VT>(s, L, rr, yr, m2 * (1.0 + 3.0 * U32), m2);
     if (pe.cert <= a.sp.tol) s.refine = 1;
   }
-  if (!s.refine) pass_decide<VT>(s, a, m1, m1, ps);
+  if (!s.refine) {
+    pass_decide<VT>(s, a, m1, m1, ps);
+    check_stall<VT>(s, a, ps.cert);
+  }
   *sp = s;
 }
 
@@ -1414,7 +1435,7 @@ __global__ void k_schedule_full(PassArgs<VT> a) {
 // upper bounds with the exact level's margins); the preserved atoms are covered by c_m1.
 template <typename VT>
 __global__ void __launch_bounds__(CORR_THREADS) k_full_check(PassArgs<VT> a) {
-  __shared__ float s_m[CORR_THREADS / 32];
+  __shared__ double s_m[CORR_THREADS / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int B = a.sp.B;
   const int total = a.offsets2[B];
@@ -1433,19 +1454,29 @@ __global__ void __launch_bounds__(CORR_THREADS) k_full_check(PassArgs<VT> a) {
     const VT* rho = a.Rho + (int64_t)b * a.ldN;
     const uint8_t* mk = a.mask + (int64_t)b * a.K;
     const float nrho_f = s.c_nrho_ru;
+    // an atom whose loose bound reaches the preserved atoms' maximum could decide the scaling:
+    // recompute it from the FP32 data with error-free products (tight bound), as k_refine does
+    const bool tighten = sizeof(VT) == 4 && L.kind == LK_F32;
+    const float T_f = __double2float_rd(s.c_m1);
     const int64_t j0 = (int64_t)chunk * CH, j1 = min((int64_t)a.K, j0 + CH);
-    float m = 0.f;
+    double m = 0.0;
     for (int64_t j = j0 + wid; j < j1; j += CORR_THREADS / 32) {
       if (mk[j]) continue;   // warp-uniform: every lane reads the same flag
       const float g = (float)warp_atom_dot_fast<VT>(L, j, (int)a.ldN, rho, lane);
-      m = fmaxf(m, __fmaf_ru(L.epsr32_simt[j], nrho_f, __fmul_ru(fabsf(g), 1.0000004f)));
+      const float ub = __fmaf_ru(L.epsr32_simt[j], nrho_f, __fmul_ru(fabsf(g), 1.0000004f));
+      if (tighten && ub > T_f) {   // warp-uniform: g is the same in every lane
+        const double gd = warp_atom_dot(L, j, (int)a.ldN, reinterpret_cast<const float*>(rho), nullptr, lane);
+        m = fmax(m, fabs(gd) * (1.0 + 3.0 * U32) + L.gam_tight * L.kappa[j] * (double)nrho_f);
+      } else {
+        m = fmax(m, (double)ub);
+      }
     }
     if (lane == 0) s_m[wid] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-      float t = 0.f;
-      for (int w = 0; w < CORR_THREADS / 32; ++w) t = fmaxf(t, s_m[w]);
-      a.part_full[(int64_t)b * a.nch + chunk] = (double)t;
+      double t = 0.0;
+      for (int w = 0; w < CORR_THREADS / 32; ++w) t = fmax(t, s_m[w]);
+      a.part_full[(int64_t)b * a.nch + chunk] = t;
     }
     __syncthreads();
   }
@@ -1779,7 +1810,7 @@ __global__ void k_outputs(PassArgs<VT> a, float* __restrict__ Xf, double* __rest
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (gaps) gaps[b] = s.gap;
-    if (status) status[b] = s.status;
+    if (status) status[b] = s.status == LASSO_ST_SATURATED ? LASSO_ERR_MAXITER : s.status;
     if (iters) iters[b] = s.iters;
   }
 }
@@ -1994,6 +2025,9 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   pa.sp.B = (int)B;
   pa.sp.chunk = B >= 64 ? 4 * CORR_CHUNK : CORR_CHUNK;
   pa.sp.full_gap = o.full_gap ? 1 : 0;
+  // saturation of the FP32 iterates on the exact level: 200 passes without a 2 % better
+  // certificate (a converging FISTA improves far faster), then the FP64 solve takes over
+  pa.sp.stall_passes = sizeof(VT) == 4 && o.fp64_fallback && d->exact_kind == LK_F32 ? 200 : 0;
   fill_pass_args(pa, w, d);
   const size_t vs = sizeof(VT);
   const size_t BK = (size_t)B * d->K;
@@ -2168,6 +2202,126 @@ extern "C" void lasso_opts_default(lasso_opts* o) {
   o->profile = 0;
   o->full_gap = 1;
   o->tc_exact = 0;
+  o->fp64_fallback = 1;
+}
+
+// ------------------------------------------------------------------ FP64 second solve
+
+static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats);
+
+__global__ void k_find_saturated(const SigState* __restrict__ st, int64_t B, int32_t* __restrict__ idx,
+                                 int32_t* __restrict__ count) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < B && st[b].status == LASSO_ST_SATURATED) idx[atomicAdd(count, 1)] = (int32_t)b;
+}
+
+// Rows of the saturated signals (y as given, lambda as resolved) for the second solve.
+__global__ void k_gather_saturated(const SigState* __restrict__ st, const float* __restrict__ Yf,
+                                   const double* __restrict__ Yd, int64_t N, const int32_t* __restrict__ idx, int n,
+                                   float* __restrict__ Ysub, double* __restrict__ lam) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const int64_t b = idx[i];
+  for (int64_t c = threadIdx.x; c < N; c += blockDim.x)
+    Ysub[(int64_t)i * N + c] = Yf ? Yf[b * N + c] : (float)Yd[b * N + c];
+  if (threadIdx.x == 0) lam[i] = st[b].lam;
+}
+
+__global__ void k_scatter_saturated(const int32_t* __restrict__ idx, int n, int64_t K, const float* __restrict__ Xs,
+                                    const double* __restrict__ gs, const int32_t* __restrict__ ss,
+                                    const int32_t* __restrict__ is, float* __restrict__ X, double* __restrict__ gaps,
+                                    int32_t* __restrict__ status, int32_t* __restrict__ iters) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const int64_t b = idx[i];
+  if (X)
+    for (int64_t j = threadIdx.x; j < K; j += blockDim.x) X[b * K + j] = Xs[(int64_t)i * K + j];
+  if (threadIdx.x == 0) {
+    if (gaps) gaps[b] = gs[i];
+    if (status) status[b] = ss[i];
+    if (iters) iters[b] += is[i];
+  }
+}
+
+// Signals whose FP32 iterates saturated on the exact level are solved again from scratch with
+// FP64 iterates and the FP64-accumulation rung (as final_fp64 does), with the lambda each one
+// was solved for; their outputs replace the FP32 ones.
+static int fp64_fallback(lasso_dict* d, Workspace* w, SolveIO& io, lasso_stats* stats) {
+  const int64_t B = io.B, N = d->N, K = d->K;
+  cudaStream_t st = io.stream ? io.stream : w->stream;
+  int32_t *idx = nullptr, *cnt = nullptr, *ss = nullptr, *is = nullptr;
+  float *Ys = nullptr, *Xs = nullptr;
+  double *lam = nullptr, *gs = nullptr;
+  auto release = [&]() {
+    cudaFree(idx);
+    cudaFree(cnt);
+    cudaFree(ss);
+    cudaFree(is);
+    cudaFree(Ys);
+    cudaFree(Xs);
+    cudaFree(lam);
+    cudaFree(gs);
+  };
+  if (cudaMalloc(&idx, B * 4) != cudaSuccess || cudaMalloc(&cnt, 4) != cudaSuccess) {
+    release();
+    return LASSO_ERR_NOMEM;
+  }
+  int n = 0;
+  LASSO_CUDA_TRY(cudaMemsetAsync(cnt, 0, 4, st));
+  k_find_saturated<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(w->st, B, idx, cnt);
+  LASSO_CUDA_TRY(cudaMemcpyAsync(&n, cnt, 4, cudaMemcpyDeviceToHost, st));
+  LASSO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (n == 0) {
+    release();
+    return LASSO_OK;
+  }
+  if (cudaMalloc(&Ys, (size_t)n * N * 4) != cudaSuccess || cudaMalloc(&lam, (size_t)n * 8) != cudaSuccess ||
+      cudaMalloc(&Xs, (size_t)n * K * 4) != cudaSuccess || cudaMalloc(&gs, (size_t)n * 8) != cudaSuccess ||
+      cudaMalloc(&ss, (size_t)n * 4) != cudaSuccess || cudaMalloc(&is, (size_t)n * 4) != cudaSuccess) {
+    release();
+    return LASSO_ERR_NOMEM;
+  }
+  k_gather_saturated<<<n, 256, 0, st>>>(w->st, io.Yf, io.Yd, N, idx, n, Ys, lam);
+  LASSO_CUDA_TRY(cudaGetLastError());
+  LASSO_CUDA_TRY(cudaStreamSynchronize(st));
+  SolveIO sub = io;
+  sub.Yf = Ys;
+  sub.Yd = nullptr;
+  sub.lambdas = lam;
+  sub.B = n;
+  sub.opts.final_fp64 = 1;
+  sub.opts.lambda_relative = 0;
+  sub.opts.fp64_fallback = 0;
+  sub.Xf = Xs;
+  sub.gaps = gs;
+  sub.status = ss;
+  sub.iters = is;
+  lasso_stats sst;
+  const int rc = solve_common(d, sub, stats ? &sst : nullptr);
+  if (rc == LASSO_OK) {
+    k_scatter_saturated<<<n, 256, 0, st>>>(idx, n, K, Xs, gs, ss, is, io.Xf, io.gaps, io.status, io.iters);
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+      release();
+      set_last_error(cudaGetErrorString(ce), __FILE__, __LINE__);
+      return LASSO_ERR_CUDA;
+    }
+    if (stats) {
+      stats->passes = std::max(stats->passes, sst.passes);
+      for (int l = 0; l < MAX_LEVELS; ++l) stats->level_passes[l] += sst.level_passes[l];
+      stats->launches += sst.launches;
+      for (int q = 0; q < 6; ++q) {
+        stats->kernel_launches[q] += sst.kernel_launches[q];
+        stats->kernel_ms[q] += sst.kernel_ms[q];
+        stats->kernel_bytes[q] += sst.kernel_bytes[q];
+      }
+      stats->seconds += sst.seconds;
+      stats->fp64_resolved = n;
+    }
+  }
+  release();
+  return rc;
 }
 
 static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
@@ -2182,7 +2336,9 @@ static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
   int rc = get_ws(d, io.B, vt_double, &w);
   if (rc) return rc;
   if (vt_double) return run_solve<double>(d, w, io, stats);
-  return run_solve<float>(d, w, io, stats);
+  rc = run_solve<float>(d, w, io, stats);
+  if (rc != LASSO_OK || !io.opts.fp64_fallback || d->exact_kind != LK_F32) return rc;
+  return fp64_fallback(d, w, io, stats);
 }
 
 extern "C" int lasso_solve_batch(lasso_dict* d, const float* d_Y, const double* d_lambdas, int64_t B, double tol,
@@ -2258,9 +2414,17 @@ extern "C" int lasso_solve(lasso_dict* d, const double* y, double lambda, double
   cudaFree(dy);
   cudaFree(dl);
   if (rc != LASSO_OK && rc != LASSO_ERR_MAXITER && rc != LASSO_ERR_TIMEOUT && rc != LASSO_WARN_AUDIT) return rc;
-  Workspace* w = d->ws;
+  // the solve's workspace; a signal finished by the FP64 second solve lives in the FP64 one
+  const bool vt_double = d->exact_kind == LK_F64 || io.opts.final_fp64;
+  Workspace* w = vt_double ? d->ws64 : d->ws;
+  if (!w) return LASSO_ERR_CUDA;
   SigState s;
   if (cudaMemcpy(&s, w->st, sizeof(s), cudaMemcpyDeviceToHost) != cudaSuccess) return LASSO_ERR_CUDA;
+  if (!vt_double && s.status == LASSO_ST_SATURATED && io.opts.fp64_fallback && d->ws64) {
+    w = d->ws64;
+    if (cudaMemcpy(&s, w->st, sizeof(s), cudaMemcpyDeviceToHost) != cudaSuccess) return LASSO_ERR_CUDA;
+  }
+  if (s.status == LASSO_ST_SATURATED) s.status = LASSO_ERR_MAXITER;
   if (w->vt_double) {
     if (cudaMemcpy(x, w->Xout, d->K * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return LASSO_ERR_CUDA;
   } else {

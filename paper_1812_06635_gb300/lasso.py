@@ -42,6 +42,7 @@ class Stats:
     kernel_ms: list = None
     kernel_bytes: list = None
     level_atoms: list = None
+    fp64_resolved: int = 0
 
     KINDS = ("residual", "corr", "screen", "schedule", "kron", "tc_gemm")
 
@@ -50,7 +51,7 @@ class Stats:
         return Stats(int(s.passes), [int(v) for v in s.level_passes], int(s.kept_final), float(s.lambda_max),
                      float(s.lambda_), float(s.seconds), int(s.launches), [int(v) for v in s.kernel_launches],
                      [float(v) for v in s.kernel_ms], [float(v) for v in s.kernel_bytes],
-                     [float(v) for v in s.level_atoms])
+                     [float(v) for v in s.level_atoms], int(s.fp64_resolved))
 
 
 def _ptr(a) -> C.c_void_p:

@@ -306,6 +306,30 @@ def test_fast_l1_kronecker_ladder():
         assert np.linalg.norm(r.x - xs) <= 1e-5 * max(np.linalg.norm(xs), 1e-30)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_structured_polish_matches_brute_force(seed):
+    """The operator form of the KKT polish (support columns formed from the Kronecker factors,
+    KKT checked with the structured adjoint) reproduces the 3^K sign enumeration (K = 8)."""
+    w = S.kron_small(R=2, N1=3, K1=2, N2=5, K2=4, n_signals=1, seed=seed, p=0.3)
+    d = D.kron_unit_scale(w.Bf, w.Cf)
+    op = D.KronDict(w.Bf, w.Cf, d)
+    A = op.dense()
+    y = w.Y[0]
+    lam = max(w.lam_ratio[0], 0.3) * L.lambda_max(A.T @ y)
+    xb = SV.brute_force(A, y, lam)
+    r = SV.fast_l1([D.kron_level(w.Bf, w.Cf, d, 2)], np.linalg.norm(A, axis=0), y, lam, 1e-15, max_iter=400000)
+    x, ok = SV.kkt_polish_op(op, y, lam, r.x, thresh=1e-9)
+    assert ok
+    np.testing.assert_allclose(x, xb, rtol=0, atol=1e-10)
+    # a wrong support is rejected by the structured KKT check
+    if np.count_nonzero(xb) >= 1:
+        wrong = xb.copy()
+        wrong[np.flatnonzero(xb)[0]] = 0.0
+        if np.count_nonzero(wrong):
+            _, ok_wrong = SV.kkt_polish_op(op, y, lam, wrong)
+            assert not ok_wrong
+
+
 def test_dynamic_safe_rule_and_ista():
     """Stable Dynamic Safe (Table I) and ISTA reach the same minimiser, safely."""
     A, y, lam = _small_problem(30, 90, 6, 0.6)
