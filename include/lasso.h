@@ -144,6 +144,11 @@ typedef struct {
                                 with FP64 iterates and an FP64-accumulation rung, as final_fp64
                                 does; its outputs replace the FP32 ones.  0: such a signal ends
                                 with LASSO_ERR_MAXITER.                                          */
+    int autotune;            /* 1 (default): before the first FP32 batch of a size class (B rounded
+                                up to a power of two), time the correlation pass for atom chunks
+                                of 64 / 128 / 256 and 4 / 8 / 16 blocks per SM on a synthetic
+                                exact-level state (K / 8 preserved atoms per signal) and keep the
+                                fastest for the dictionary; 0: 128-atom chunks, 8 blocks per SM */
 } lasso_opts;
 
 /* Fill *opts with the defaults above. */
@@ -166,6 +171,8 @@ typedef struct {
     double kernel_bytes[6];
     double level_atoms[8];   /* sum over passes and signals of |A_t| on each level              */
     int64_t fp64_resolved;   /* signals solved again with FP64 iterates (opts.fp64_fallback)     */
+    int64_t corr_chunk;      /* atoms per correlation work item used by the solve              */
+    int64_t corr_blocks_per_sm; /* correlation grid, in blocks per SM                           */
 } lasso_stats;
 
 /* Solve one signal (host buffers).  y: N values (rounded to the exact level's precision on

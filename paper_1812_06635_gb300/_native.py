@@ -30,6 +30,7 @@ class LassoOpts(C.Structure):
         ("full_gap", C.c_int),
         ("tc_exact", C.c_int),
         ("fp64_fallback", C.c_int),
+        ("autotune", C.c_int),
     ]
 
 
@@ -47,6 +48,8 @@ class LassoStats(C.Structure):
         ("kernel_bytes", C.c_double * 6),
         ("level_atoms", C.c_double * 8),
         ("fp64_resolved", C.c_int64),
+        ("corr_chunk", C.c_int64),
+        ("corr_blocks_per_sm", C.c_int64),
     ]
 
 

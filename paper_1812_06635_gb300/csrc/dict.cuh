@@ -1,6 +1,8 @@
 // Host-side dictionary object shared by the library's translation units.
 #pragma once
 
+#include <map>
+
 #include <vector>
 
 #include "common.cuh"
@@ -55,6 +57,7 @@ struct lasso_dict {
   lasso::HostLevel rung64;             // FP64-accumulation rung on FP32 exact data (lazy)
   double L = 0.0;
   bool prepared = false;
+  std::map<int, std::pair<int, int>> corr_tune;   // log2(B) class -> (chunk, blocks per SM)
   lasso::Workspace* ws = nullptr;     // FP32-iterate solves
   lasso::Workspace* ws64 = nullptr;   // FP64-iterate solves
 };

@@ -1957,6 +1957,86 @@ static int pass_launches(bool has_kron, bool full_gap, int n_tc) {
   return (has_kron ? 12 : 7) + (full_gap ? 3 : 0) + 2 * n_tc;
 }
 
+// ------------------------------------------------------------------ autotuner
+
+// Synthetic exact-level state for timing the correlation pass: every signal keeps n_kept atoms
+// spread evenly over the dictionary and has a bounded pseudo-random residual.
+template <typename VT>
+__global__ void k_tune_state(PassArgs<VT> a, int n_kept) {
+  const int b = blockIdx.x;
+  int32_t* kp = kept_of(a, b, 0);
+  for (int p = threadIdx.x; p < n_kept; p += blockDim.x) kp[p] = (int32_t)(((int64_t)p * a.K) / n_kept);
+  VT* rho = a.Rho + (int64_t)b * a.ldN;
+  for (int64_t n = threadIdx.x; n < a.ldN; n += blockDim.x)
+    rho[n] = n < a.dd.N ? (VT)((float)((uint32_t)(n * 2654435761u + (uint32_t)b * 40503u) >> 22) / 1024.f - 0.5f)
+                        : (VT)0;
+  if (threadIdx.x == 0) {
+    SigState st;
+    memset(&st, 0, sizeof(st));
+    st.level = a.dd.n_levels - 1;
+    st.n_kept = n_kept;
+    st.n_chunks = (n_kept + a.sp.chunk - 1) / a.sp.chunk;
+    st.lam = 1.0;
+    st.nrho_ru = 1.f;
+    st.thr_f = 1e-3f;
+    st.beta_f = 0.5f;
+    a.st[b] = st;
+  }
+}
+
+// Atom chunk and grid of the FP32 correlation pass for a batch size class: the configuration
+// with the shortest time on the synthetic exact-level state (K / 8 preserved atoms per signal),
+// measured with CUDA events on the solve's stream; kept per dictionary.
+template <typename VT>
+static int tune_corr(lasso_dict* d, const PassArgs<VT>& pa0, int64_t B, cudaStream_t st, int* chunk, int* bps) {
+  int cls = 0;
+  while ((int64_t)1 << cls < B) ++cls;
+  auto it = d->corr_tune.find(cls);
+  if (it != d->corr_tune.end()) {
+    *chunk = it->second.first;
+    *bps = it->second.second;
+    return LASSO_OK;
+  }
+  PassArgs<VT> pa = pa0;
+  const int I = pa.dd.n_levels - 1;
+  pa.dd.lv[I].tc = 0;                       // time the gathered products themselves
+  const int n_kept = (int)std::max<int64_t>(32, d->K / 8);
+  cudaEvent_t e0, e1;
+  LASSO_CUDA_TRY(cudaEventCreate(&e0));
+  LASSO_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bc = 4 * CORR_CHUNK, bb = 8;
+  const int chunks[3] = {2 * CORR_CHUNK, 4 * CORR_CHUNK, 8 * CORR_CHUNK};
+  const int grids[3] = {4, 8, 16};
+  for (int c : chunks) {
+    pa.sp.chunk = c;
+    k_tune_state<VT><<<(unsigned)B, 256, 0, st>>>(pa, n_kept);
+    k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+    for (int g : grids) {
+      const int grid = num_sms() * g;
+      k_corr_pass<VT><<<grid, CORR_THREADS, 0, st>>>(pa);   // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3; ++r) k_corr_pass<VT><<<grid, CORR_THREADS, 0, st>>>(pa);
+      cudaEventRecord(e1, st);
+      LASSO_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      LASSO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bc = c;
+        bb = g;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  LASSO_CUDA_TRY(cudaGetLastError());
+  d->corr_tune[cls] = std::make_pair(bc, bb);
+  *chunk = bc;
+  *bps = bb;
+  return LASSO_OK;
+}
+
 template <typename VT>
 static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats* stats) {
   auto t_start = std::chrono::steady_clock::now();
@@ -2029,6 +2109,16 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   // certificate (a converging FISTA improves far faster), then the FP64 solve takes over
   pa.sp.stall_passes = sizeof(VT) == 4 && o.fp64_fallback && d->exact_kind == LK_F32 ? 200 : 0;
   fill_pass_args(pa, w, d);
+  int corr_bps = 8;
+  if constexpr (sizeof(VT) == 4) {
+    if (o.autotune && B >= 64) {
+      int c = 0, g = 0;
+      rc = tune_corr<VT>(d, pa, B, st, &c, &g);
+      if (rc) return rc;
+      pa.sp.chunk = c;
+      corr_bps = g;
+    }
+  }
   const size_t vs = sizeof(VT);
   const size_t BK = (size_t)B * d->K;
   LASSO_CUDA_TRY(cudaMemsetAsync(w->X, 0, BK * vs, st));
@@ -2047,7 +2137,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     cudaFuncSetAttribute(k_corr<VT, CORR_CERT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set[vs == 8] = true;
   }
-  const int corr_grid = num_sms() * 8;
+  const int corr_grid = num_sms() * corr_bps;
   // init: lambda_max and a^T y bounds with the most precise level
   k_schedule<VT><<<1, 1024, 0, st>>>(pa);
   k_corr<VT, CORR_INIT><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
@@ -2166,6 +2256,8 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     stats->lambda_max = hs[0].lam_max_lb;
     stats->lambda = hs[0].lam;
     stats->launches = launches;
+    stats->corr_chunk = pa.sp.chunk;
+    stats->corr_blocks_per_sm = corr_bps;
     const int per_pass[6] = {1, 1, pa.sp.full_gap ? 4 : 1, 1, has_kron ? 5 : 0, 2 * (int)tc_jobs.size()};
     for (int q = 0; q < 6; ++q) {
       stats->kernel_launches[q] = replays * (int64_t)k * per_pass[q];
@@ -2203,6 +2295,7 @@ extern "C" void lasso_opts_default(lasso_opts* o) {
   o->full_gap = 1;
   o->tc_exact = 0;
   o->fp64_fallback = 1;
+  o->autotune = 1;
 }
 
 // ------------------------------------------------------------------ FP64 second solve

@@ -43,6 +43,8 @@ class Stats:
     kernel_bytes: list = None
     level_atoms: list = None
     fp64_resolved: int = 0
+    corr_chunk: int = 0
+    corr_blocks_per_sm: int = 0
 
     KINDS = ("residual", "corr", "screen", "schedule", "kron", "tc_gemm")
 
@@ -51,7 +53,8 @@ class Stats:
         return Stats(int(s.passes), [int(v) for v in s.level_passes], int(s.kept_final), float(s.lambda_max),
                      float(s.lambda_), float(s.seconds), int(s.launches), [int(v) for v in s.kernel_launches],
                      [float(v) for v in s.kernel_ms], [float(v) for v in s.kernel_bytes],
-                     [float(v) for v in s.level_atoms], int(s.fp64_resolved))
+                     [float(v) for v in s.level_atoms], int(s.fp64_resolved), int(s.corr_chunk),
+                     int(s.corr_blocks_per_sm))
 
 
 def _ptr(a) -> C.c_void_p:
