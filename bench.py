@@ -224,6 +224,20 @@ def plain_fista(A_t, Y, lam, L, tol, max_iter=3000, check_every=10):
     return int(done.sum()), time.perf_counter() - t0, it
 
 
+def _l2_peak_gbs():
+    """Measured read bandwidth of data resident in L2 (48 MiB read 50 times in one launch with
+    16-byte loads that bypass L1; the library's probe), best of 3."""
+    import ctypes as C
+    from paper_1812_06635_gb300 import _native
+    lib = _native.load()
+    best = 0.0
+    for _ in range(3):
+        v = C.c_double()
+        if lib.lasso_probe_l2_read(48 << 20, 50, C.byref(v)) == 0:
+            best = max(best, v.value)
+    return best
+
+
 def _traffic(kind):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if the
     kernel source has not changed since (hash recorded with the counters)."""
@@ -324,6 +338,14 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "avg_launch_us": 1e3 * kms[kind] / max(1.0, klaunch[kind]),
                 "kernel_share": {names[i]: kms[i] / max(1e-9, kms.sum()) for i in range(6) if kms[i] > 0}}
+    roofline["note"] = ("algorithmic bytes count every signal's own reads of its preserved atoms; the "
+                        "dictionary stays in L2 across the batch, so DRAM traffic is far below them and the "
+                        "HBM fraction can exceed 1 (see roofline_l2)")
+    l2 = _l2_peak_gbs()
+    roofline_l2 = {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                   "kernel": names[kind],
+                   "peak_source": "measured in this run: one launch reading a 48 MiB L2-resident buffer 50 "
+                                  "times with L1-bypassing 16-byte loads (lasso_probe_l2_read), best of 3"}
     # the tensor-core stage (quantisation + tcgen05 correlation of the FP8 / BF16 levels)
     roofline_tc = None
     if kms[5] > 0:
@@ -358,7 +380,10 @@ def run_ours(args):
                 "solved_per_step": solved / args.steps, "signals_per_step": B * world,
                 "e2e": {"value": e2e_solved / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(B * w.N * 4 + B * 8),
                         "d2h_bytes_per_step": int(B * w.K * 4 + B * 8 + B * 4)},
-                "gpu_launches": int(launches), "roofline": roofline, "roofline_tensor": roofline_tc,
+                "gpu_launches": int(launches), "roofline": roofline, "roofline_l2": roofline_l2,
+                "roofline_tensor": roofline_tc,
+                "autotuned": {"corr_chunk": st.corr_chunk, "corr_blocks_per_sm": st.corr_blocks_per_sm},
+                "fp64_resolved_per_step": st.fp64_resolved,
                 "cpu_baseline": cpu, "comparator": comp,
                 "clocks": clk, "passes_max": st.passes,
                 "level_passes_per_signal": [v / B for v in st.level_passes[:3]],

@@ -108,7 +108,10 @@ int lasso_dict_level_host(const lasso_dict* dict, int level, double* eps_host, d
 void lasso_dict_destroy(lasso_dict* dict);
 
 typedef enum { LASSO_FISTA = 0, LASSO_ISTA = 1 } lasso_algo;
-typedef enum { LASSO_RULE_GAP = 0, LASSO_RULE_DST = 1 } lasso_rule;
+/* Screening rules (Table I): stable GAP Safe (Theorem 1), stable Dynamic Safe, and the Static
+ * Safe sphere B(y / lam, ||y|| |1/lam - 1/lam_max'|) of eq:static_sphere with lam_max' an upper
+ * bound of lambda_max from the certified initial pass. */
+typedef enum { LASSO_RULE_GAP = 0, LASSO_RULE_DST = 1, LASSO_RULE_STATIC = 2 } lasso_rule;
 
 typedef struct {
     double Gamma;            /* switching threshold of Algorithm 2 (default 0.5)                */
@@ -233,6 +236,12 @@ int lasso_backward(lasso_dict* dict, const float* d_Y, const float* d_X, const f
  * accumulator).  The paper has no counterpart: it checks an assumption of this build's
  * rounding model (products treated as exact there). */
 int lasso_tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel_err, double* max_err_over_bound);
+
+/* Read bandwidth (GB/s) of a buffer resident in L2 (bytes in [1 MiB, 96 MiB]), read `rounds`
+ * times by one launch with 16-byte loads that bypass L1; the roofline denominator of kernels
+ * whose operands stay in L2 across a batch.  The paper has no counterpart (hardware
+ * measurement).  Allocates and frees its buffer; synchronises the device. */
+int lasso_probe_l2_read(int64_t bytes, int rounds, double* gbs);
 
 const char* lasso_strerror(int status);
 

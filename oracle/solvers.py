@@ -33,7 +33,7 @@ import numpy as np
 from . import lasso as L
 from .dictionaries import Level, exact_level, power_iteration_sq_norm
 
-GAP, DST = "gap", "dst"
+GAP, DST, STATIC = "gap", "dst", "static"
 FISTA, ISTA = "fista", "ista"
 
 
@@ -129,10 +129,13 @@ def fast_l1(levels: list[Level], anorm: np.ndarray, y: np.ndarray, lam: float, t
             if rule == GAP:
                 Rp = L.stable_gap_radius(Gp, delta, lam)
                 mu = L.stable_sphere_test(s_p * g, eps, abs(s_p) * nrho, Rp, anorm[kept])
-            else:   # Stable Dynamic Safe with exact a^T y (Table I, fourth row, first form)
+            elif rule == DST:   # Stable Dynamic Safe with exact a^T y (Table I, fourth row, first form)
                 d2 = s_p * s_p * rr - 2.0 * s_p * yr / lam + yy / (lam * lam)
                 Rp = float(np.sqrt(max(d2, 0.0)))
                 mu = np.abs(Aty[kept]) / lam + Rp * anorm[kept]
+            else:   # Static Safe sphere (eq:static_sphere) around y / lam, with the exact a^T y
+                _, Rs = L.static_sphere(y, lam, lam_max)
+                mu = np.abs(Aty[kept]) / lam + Rs * anorm[kept]
             keep_mask = mu >= 1.0 - tau
         Rt = L.gap_safe_radius(Gt, lam)
         K_t = int(np.count_nonzero(L.sphere_test(s_t * g, Rt, lev.atnorm[kept]) >= 1.0))

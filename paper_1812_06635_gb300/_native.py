@@ -93,6 +93,7 @@ SIGNATURES = [
     ("lasso_lambda_max_noalloc", C.c_int, [P, P, I64, P, P]),
     ("lasso_backward", C.c_int, [P, P, P, P, I64, P, P, P]),
     ("lasso_tc_selftest", C.c_int, [C.c_int, I64, I64, I64, PD, PD]),
+    ("lasso_probe_l2_read", C.c_int, [I64, C.c_int, PD]),
     ("lasso_strerror", C.c_char_p, [C.c_int]),
     ("lasso_build_info", C.c_char_p, []),
 ]

@@ -978,7 +978,14 @@ __device__ void pass_decide(SigState& s, const PassArgs<VT>& a, double m1_bulk, 
   s.act = action;
   s.t_abs_sp = fabs(sp_);
   s.t_c_eps = fabs(sp_) * nrho;
-  s.t_Rs = a.sp.rule == LASSO_RULE_GAP ? s.Rp : sqrt(fmax(d2, 0.0)) * (1.0 + 4.0 * U64);
+  if (a.sp.rule == LASSO_RULE_GAP) {
+    s.t_Rs = s.Rp;
+  } else if (a.sp.rule == LASSO_RULE_DST) {
+    s.t_Rs = sqrt(fmax(d2, 0.0)) * (1.0 + 4.0 * U64);
+  } else {
+    // Static Safe sphere around y / lam (eq:static_sphere); lam_max_ub >= lambda_max
+    s.t_Rs = s.ynorm * fmax(inv_lam - 1.0 / s.lam_max_ub, 0.0) * (1.0 + 8.0 * U64);
+  }
   s.t_abs_st = ps.abs_st;
   s.t_Rt = ps.Rt;
   s.t_inv_lam = inv_lam * (1.0 + 2.0 * U64);
@@ -2419,6 +2426,9 @@ static int fp64_fallback(lasso_dict* d, Workspace* w, SolveIO& io, lasso_stats* 
 
 static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
   if (!d || io.B <= 0 || !(io.tol > 0.0)) return LASSO_ERR_INVALID_ARG;
+  if (io.opts.rule < LASSO_RULE_GAP || io.opts.rule > LASSO_RULE_STATIC || io.opts.algo < LASSO_FISTA ||
+      io.opts.algo > LASSO_ISTA)
+    return LASSO_ERR_INVALID_ARG;
   if (d->ldN > 24576) return LASSO_ERR_UNSUPPORTED;
   if (!d->prepared) {
     int rc = dict_prepare(d, 0.0);

@@ -13,7 +13,7 @@ from . import _native as nat
 
 LEVEL_BF16, LEVEL_FP8, LEVEL_KRON, LEVEL_F32 = 2, 3, 4, 5
 FISTA, ISTA = 0, 1
-RULE_GAP, RULE_DST = 0, 1
+RULE_GAP, RULE_DST, RULE_STATIC = 0, 1, 2
 STATUS = {0: "ok", -1: "invalid_arg", -2: "cuda", -3: "nonfinite", -4: "maxiter", -5: "timeout",
           -6: "unsupported", -7: "nomem", 1: "warn_audit"}
 

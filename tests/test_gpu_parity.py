@@ -76,8 +76,9 @@ def test_orthonormal_soft_threshold(pkg):
     np.testing.assert_allclose(x, OL.soft_threshold(Q.T @ y, lam), atol=1e-10)
 
 
-@pytest.mark.parametrize("algo,rule", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("algo,rule", [(1, 0), (0, 1), (1, 1), (0, 2), (1, 2)])
 def test_ista_and_dynamic_safe(pkg, algo, rule):
+    """ISTA / FISTA with the stable GAP, Dynamic Safe and Static Safe rules (Table I)."""
     w = S.c1()
     A, y = w.A, w.Y[0]
     lam = 0.5 * OL.lambda_max(A.T @ y)

@@ -330,6 +330,23 @@ def test_structured_polish_matches_brute_force(seed):
             assert not ok_wrong
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_static_sphere_contains_theta_star(seed):
+    """The Static Safe sphere (eq:static_sphere) contains the dual solution theta* = (y - A x*)/lam
+    (y / lam_max is dual feasible and theta* is the projection of y / lam on the feasible set), and
+    the Static rule reaches the same minimiser while rejecting only atoms outside the support."""
+    A, y, lam = _small_problem(30, 80, seed, 0.7)
+    xs, ts = _theta_star(A, y, lam)
+    c, R = L.static_sphere(y, lam, L.lambda_max(A.T @ y))
+    assert np.linalg.norm(ts - c) <= R * (1 + 1e-12)
+    r = SV.fast_l1([D.exact_level(A)], np.linalg.norm(A, axis=0), y, lam, 1e-13, rule=SV.STATIC, trace=True,
+                   max_iter=200000)
+    assert r.converged
+    for _, rej in r.rejected_trace:
+        assert np.all(xs[rej] == 0.0)
+    assert np.linalg.norm(r.x - xs) <= 1e-5 * max(np.linalg.norm(xs), 1e-30)
+
+
 def test_dynamic_safe_rule_and_ista():
     """Stable Dynamic Safe (Table I) and ISTA reach the same minimiser, safely."""
     A, y, lam = _small_problem(30, 90, 6, 0.6)
