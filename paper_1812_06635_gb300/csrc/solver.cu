@@ -852,6 +852,82 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr_pass(PassArgs<VT> a) {
   if (a.alg_bytes && lane == 0 && bytes > 0.f) atomicAdd(&a.alg_bytes[1], (double)bytes);
 }
 
+// The initial pass on the tensor cores: g^_j ~ a~_j^T y for every atom from a batched product
+// with a tensor-core level (Gfull), bounded by the level's error (eps_j, the accumulation and
+// the quantisation of y).  Every atom whose upper bound reaches the largest lower bound could
+// attain lambda_max = max_j |a_j^T y| (eq:DefLMax); those are recomputed from the exact data with
+// error-free products, so lambda_max keeps the bounds of the exact initial pass.  The other
+// atoms keep their tensor-core upper bounds of |a_j^T y| (Dynamic / Static Safe rules).
+template <typename VT>
+__global__ void __launch_bounds__(256) k_init_tc(PassArgs<VT> a, int lvl) {
+  const int b = blockIdx.x;
+  SigState* sp = a.st + b;
+  __shared__ int s_go;
+  __shared__ float s_lb[8];
+  __shared__ double s_m1[8], s_m2[8];
+  if (threadIdx.x == 0) s_go = !sp->done;
+  __syncthreads();
+  if (!s_go) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const LevelDev& Lq = a.dd.lv[lvl];
+  const LevelDev& Lx = a.dd.lv[a.dd.n_levels - 1];
+  const int64_t K = a.K;
+  const float* g = a.Gfull + (int64_t)b * K;
+  float* c0 = a.c0ub + (int64_t)b * K;
+  const double ynorm = sp->ynorm;
+  const float yn_f = __double2float_ru(ynorm);
+  const float dq_f = __double2float_ru(sp->dq * 1.001);
+  // upper bounds of |a_j^T y| for every atom, and the largest lower bound
+  float lbm = 0.f;
+  for (int64_t j = threadIdx.x; j < K; j += 256) {
+    const float ag = fabsf(g[j]);
+    const float err = __fmaf_ru(Lq.kappa32[j], dq_f, __fmul_ru(Lq.epsr32[j], yn_f));
+    c0[j] = __fadd_ru(__fmul_ru(ag, 1.0000005f), err);
+    lbm = fmaxf(lbm, __fsub_rd(__fmul_rd(ag, 0.9999995f), err));
+  }
+  lbm = warp_max_f(lbm);
+  if (lane == 0) s_lb[wid] = lbm;
+  __syncthreads();
+  float T = 0.f;
+  for (int w = 0; w < 8; ++w) T = fmaxf(T, s_lb[w]);
+  // candidates: recomputed with error-free products on the exact atoms
+  const float* yv = reinterpret_cast<const float*>(a.Yw + (int64_t)b * a.ldN);
+  double m1 = 0.0, m2 = 0.0;
+  for (int64_t base = (int64_t)wid * 32; base < K; base += 256) {
+    const int64_t j = base + lane;
+    const bool cand = j < K && c0[j] >= T;
+    unsigned m = __ballot_sync(0xffffffffu, cand);
+    while (m) {
+      const int l = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t jj = base + l;
+      const double gx = warp_atom_dot(Lx, jj, (int)a.ldN, yv, nullptr, lane);
+      const double ub = fabs(gx) * (1.0 + 4.0 * U64) + (Lx.eps[jj] + Lx.gam_tight * Lx.kappa[jj]) * ynorm;
+      m1 = fmax(m1, ub);
+      m2 = fmax(m2, fabs(gx));
+      if (lane == 0) c0[jj] = __double2float_ru(ub);
+    }
+  }
+  if (lane == 0) {
+    s_m1[wid] = m1;
+    s_m2[wid] = m2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < 8; ++w) {
+      m1 = fmax(m1, s_m1[w]);
+      m2 = fmax(m2, s_m2[w]);
+    }
+  }
+  // the initial-pass maxima as k_init_finish reads them (first chunk; the others empty)
+  const int nch = (int)((K + a.sp.chunk - 1) / a.sp.chunk);
+  for (int c = threadIdx.x; c < nch; c += 256) {
+    double* pc = a.part_corr + ((int64_t)b * a.nch + c) * 2;
+    pc[0] = c == 0 ? m1 : 0.0;
+    pc[1] = c == 0 ? m2 : 0.0;
+  }
+}
+
 template <typename VT>
 __global__ void k_init_finish(PassArgs<VT> a, int lambda_relative) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1054,7 +1130,10 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
   s.e_m1 = m1;
   s.e_m2 = m2;
   s.refine = 0;
-  if (sizeof(VT) == 4 && L.kind == LK_F32 && s.level == I && ps.cert > a.sp.tol && rr > 0.0 && m2 > 0.0) {
+  // (with the full-dictionary stop, only a pass that may take a snapshot needs the tight value)
+  const bool may_stop = !a.sp.full_gap || (!s.pending && s.iters >= s.next_check);
+  if (sizeof(VT) == 4 && L.kind == LK_F32 && s.level == I && ps.cert > a.sp.tol && rr > 0.0 && m2 > 0.0 &&
+      may_stop) {
     // would the certificate meet tol with the tight products?  then k_screen tightens it
     const PassScalars pe = pass_scalars<VT>(s, L, rr, yr, m2 * (1.0 + 3.0 * U32), m2);
     if (pe.cert <= a.sp.tol) s.refine = 1;
@@ -1544,10 +1623,11 @@ __global__ void k_full_finish(PassArgs<VT> a) {
 // bounds add.  The split level adds c2 ||r2|| for the product a2^T r2 it leaves out.  FP32
 // iterates: exact differences (BF16, split) or one rounding (E4M3), squares summed upward.
 template <typename VT>
-__global__ void __launch_bounds__(256) k_quant_rho(PassArgs<VT> a, int lvl, int fp8) {
+__global__ void __launch_bounds__(256) k_quant_rho(PassArgs<VT> a, int lvl, int fp8, int identity = 0) {
   const int b = blockIdx.x;
   const int B = a.sp.B;
-  const int slot = a.tc_slot[(int64_t)lvl * B + b];
+  // identity: every live signal in its own row (the initial pass, rho = y)
+  const int slot = identity ? (a.st[b].done ? -1 : b) : a.tc_slot[(int64_t)lvl * B + b];
   if (slot < 0) return;
   __shared__ float s_max[8];
   __shared__ double s_sum[2][8];
@@ -2146,13 +2226,25 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   }
   const int corr_grid = num_sms() * corr_bps;
   // init: lambda_max and a^T y bounds with the most precise level
+  LASSO_CUDA_TRY(cudaMemsetAsync(w->tc_err, 0, 4, st));
   k_schedule<VT><<<1, 1024, 0, st>>>(pa);
-  k_corr<VT, CORR_INIT><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
+  // initial pass: on the tensor cores when a BF16 (else FP8) level runs there, else exact products
+  const TcJob* init_job = nullptr;
+  for (const TcJob& j : tc_jobs)
+    if (!pa.dd.lv[j.lvl].split && (!init_job || (init_job->fp8 && !j.fp8))) init_job = &j;
+  if (sizeof(VT) == 4 && init_job) {
+    LASSO_CUDA_TRY(cudaMemcpyAsync(w->Rho, w->Yw, (size_t)B * d->ldN * vs, cudaMemcpyDeviceToDevice, st));
+    k_quant_rho<VT><<<(unsigned)B, 256, 0, st>>>(pa, init_job->lvl, init_job->fp8, 1);
+    tc_launch_corr(init_job->ops, pa.K, B, pa.ldN, init_job->scale, init_job->rsig, nullptr, nullptr, pa.Gfull,
+                   w->tc_err, st);
+    k_init_tc<VT><<<(unsigned)B, 256, 0, st>>>(pa, init_job->lvl);
+  } else {
+    k_corr<VT, CORR_INIT><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
+  }
   k_init_finish<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa, o.lambda_relative);
   k_schedule<VT><<<1, 1024, 0, st>>>(pa);
   LASSO_CUDA_TRY(cudaGetLastError());
   LASSO_CUDA_TRY(cudaMemsetAsync(w->alg_bytes, 0, 16 * sizeof(double), st));
-  LASSO_CUDA_TRY(cudaMemsetAsync(w->tc_err, 0, 4, st));
   // capture k passes
   const int k = std::max(1, o.passes_per_sync);
   cudaGraph_t graph = nullptr;
