@@ -20,6 +20,7 @@
 namespace lasso {
 
 constexpr int SCREEN_THREADS = 256;
+constexpr int FULL_SET = MAX_LEVELS - 1;    // slot list of the signals under the full-dictionary check
 constexpr int CORR_THREADS = 256;
 constexpr int RES_ROWS = RES_THREADS * 4;   // rows per residual block
 constexpr int GEMM_T = 64;                  // tile of the Kronecker small GEMMs
@@ -1481,8 +1482,12 @@ __global__ void __launch_bounds__(SCREEN_THREADS, 4) k_screen(PassArgs<VT> a) {
 template <typename VT>
 __global__ void k_schedule_full(PassArgs<VT> a) {
   __shared__ int sh_sum[32];
-  __shared__ int carry;
-  if (threadIdx.x == 0) carry = 0;
+  __shared__ int sh_cnt[32];
+  __shared__ int carry, carry2;
+  if (threadIdx.x == 0) {
+    carry = 0;
+    carry2 = 0;
+  }
   __syncthreads();
   const int B = a.sp.B;
   const int nchk = (int)((a.K + a.sp.chunk - 1) / a.sp.chunk);
@@ -1510,11 +1515,33 @@ __global__ void k_schedule_full(PassArgs<VT> a) {
     }
     __syncthreads();
     if (b < B) a.offsets2[b] = carry + (wid ? sh_sum[wid - 1] : 0) + v - items;
+    // slot of the signal among those under check (operand rows of the tensor-core check)
+    const unsigned bal = __ballot_sync(0xffffffffu, items > 0);
+    if (lane == 0) sh_cnt[wid] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = carry2;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+        const int c = sh_cnt[w2];
+        sh_cnt[w2] = acc;
+        acc += c;
+      }
+      carry2 = acc;
+    }
+    __syncthreads();
+    if (b < B) {
+      const int slot = sh_cnt[wid] + __popc(bal & ((1u << lane) - 1u));
+      a.tc_slot[(int64_t)FULL_SET * B + b] = items > 0 ? slot : -1;
+      if (items > 0) a.tc_list[(int64_t)FULL_SET * B + slot] = b;
+    }
     __syncthreads();
     if (threadIdx.x == 0) carry += sh_sum[(blockDim.x >> 5) - 1];
     __syncthreads();
   }
-  if (threadIdx.x == 0) a.offsets2[B] = carry;
+  if (threadIdx.x == 0) {
+    a.offsets2[B] = carry;
+    a.counters[8 + FULL_SET] = carry2;
+  }
 }
 
 // Correlations of the rejected atoms with the snapshot residual (fast products, rigorous
@@ -1566,6 +1593,58 @@ __global__ void __launch_bounds__(CORR_THREADS) k_full_check(PassArgs<VT> a) {
     }
     __syncthreads();
   }
+}
+
+// The full-dictionary check with the tensor cores: the rejected atoms' correlations with the
+// snapshot residual come from the batched product of a tensor-core level (Gfull), bounded by
+// that level's error; a rejected atom whose bound reaches the preserved atoms' maximum is
+// recomputed from the exact data with error-free products.  One block per signal under check.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_full_check_tc(PassArgs<VT> a, int lvl) {
+  const int b = blockIdx.x;
+  const SigState& s = a.st[b];
+  if (s.done || !s.pending) return;
+  __shared__ double s_m[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const LevelDev& Lq = a.dd.lv[lvl];
+  const LevelDev& Lx = a.dd.lv[a.dd.n_levels - 1];
+  const int64_t K = a.K;
+  const float* g = a.Gfull + (int64_t)b * K;
+  const uint8_t* mk = a.mask + (int64_t)b * K;
+  const float nrho_f = s.c_nrho_ru;
+  const float dq_f = __double2float_ru(s.dq * 1.001);
+  const float T_f = __double2float_rd(s.c_m1);
+  const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
+  double m = 0.0;
+  for (int64_t base = (int64_t)wid * 32; base < K; base += 256) {
+    const int64_t j = base + lane;
+    bool cand = false;
+    if (j < K && !mk[j]) {
+      const float err = __fmaf_ru(Lq.kappa32[j], dq_f, __fmul_ru(Lq.epsr32[j], nrho_f));
+      const float ub = __fadd_ru(__fmul_ru(fabsf(g[j]), 1.0000005f), err);
+      if (ub > T_f) cand = true;
+      else m = fmax(m, (double)ub);
+    }
+    unsigned msk = __ballot_sync(0xffffffffu, cand);
+    while (msk) {
+      const int l = __ffs(msk) - 1;
+      msk &= msk - 1;
+      const int64_t jj = base + l;
+      const double gx = warp_atom_dot(Lx, jj, (int)a.ldN, rho, nullptr, lane);
+      m = fmax(m, fabs(gx) * (1.0 + 3.0 * U32) + Lx.gam_tight * Lx.kappa[jj] * (double)nrho_f);
+    }
+  }
+  m = warp_max(m);
+  if (lane == 0) s_m[wid] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t = fmax(t, s_m[w]);
+    s_m[0] = t;
+  }
+  __syncthreads();
+  const int nchk = (int)((K + a.sp.chunk - 1) / a.sp.chunk);
+  for (int c = threadIdx.x; c < nchk; c += 256) a.part_full[(int64_t)b * a.nch + c] = c == 0 ? s_m[0] : 0.0;
 }
 
 // Full-dictionary gap of the snapshot point; stop (and return it) when it meets tol.
@@ -1623,11 +1702,13 @@ __global__ void k_full_finish(PassArgs<VT> a) {
 // bounds add.  The split level adds c2 ||r2|| for the product a2^T r2 it leaves out.  FP32
 // iterates: exact differences (BF16, split) or one rounding (E4M3), squares summed upward.
 template <typename VT>
-__global__ void __launch_bounds__(256) k_quant_rho(PassArgs<VT> a, int lvl, int fp8, int identity = 0) {
+__global__ void __launch_bounds__(256) k_quant_rho(PassArgs<VT> a, int lvl, int fp8, int slot_set = -2) {
   const int b = blockIdx.x;
   const int B = a.sp.B;
-  // identity: every live signal in its own row (the initial pass, rho = y)
-  const int slot = identity ? (a.st[b].done ? -1 : b) : a.tc_slot[(int64_t)lvl * B + b];
+  // rows: the level's own slots (slot_set -2), every live signal in its own row (-1: the initial
+  // pass, rho = y), or the slots of another list (the signals under the full-dictionary check)
+  const int slot = slot_set == -1 ? (a.st[b].done ? -1 : b)
+                                  : a.tc_slot[(int64_t)(slot_set == -2 ? lvl : slot_set) * B + b];
   if (slot < 0) return;
   __shared__ float s_max[8];
   __shared__ double s_sum[2][8];
@@ -1975,7 +2056,7 @@ struct TcJob {
 
 template <typename VT>
 static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, int corr_grid, size_t corr_smem,
-                        cudaEvent_t* ev, const std::vector<TcJob>& tc, int* tc_err) {
+                        cudaEvent_t* ev, const std::vector<TcJob>& tc, int* tc_err, const TcJob* full_job) {
   const int B = pa.sp.B;
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   if (has_kron) {
@@ -2032,7 +2113,14 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   k_screen<VT><<<B, SCREEN_THREADS, 0, st>>>(pa);
   if (pa.sp.full_gap) {
     k_schedule_full<VT><<<1, 1024, 0, st>>>(pa);
-    k_full_check<VT><<<corr_grid, CORR_THREADS, 0, st>>>(pa);
+    if (full_job) {
+      k_quant_rho<VT><<<B, 256, 0, st>>>(pa, full_job->lvl, full_job->fp8, FULL_SET);
+      tc_launch_corr(full_job->ops, pa.K, B, pa.ldN, full_job->scale, full_job->rsig,
+                     pa.tc_list + (int64_t)FULL_SET * B, pa.counters + 8 + FULL_SET, pa.Gfull, tc_err, st);
+      k_full_check_tc<VT><<<B, 256, 0, st>>>(pa, full_job->lvl);
+    } else {
+      k_full_check<VT><<<corr_grid, CORR_THREADS, 0, st>>>(pa);
+    }
     k_full_finish<VT><<<B, 128, 0, st>>>(pa);
   }
   if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
@@ -2040,8 +2128,8 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
 }
 
-static int pass_launches(bool has_kron, bool full_gap, int n_tc) {
-  return (has_kron ? 12 : 7) + (full_gap ? 3 : 0) + 2 * n_tc;
+static int pass_launches(bool has_kron, bool full_gap, int n_tc, bool tc_full) {
+  return (has_kron ? 12 : 7) + (full_gap ? (tc_full ? 5 : 3) : 0) + 2 * n_tc;
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -2234,7 +2322,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     if (!pa.dd.lv[j.lvl].split && (!init_job || (init_job->fp8 && !j.fp8))) init_job = &j;
   if (sizeof(VT) == 4 && init_job) {
     LASSO_CUDA_TRY(cudaMemcpyAsync(w->Rho, w->Yw, (size_t)B * d->ldN * vs, cudaMemcpyDeviceToDevice, st));
-    k_quant_rho<VT><<<(unsigned)B, 256, 0, st>>>(pa, init_job->lvl, init_job->fp8, 1);
+    k_quant_rho<VT><<<(unsigned)B, 256, 0, st>>>(pa, init_job->lvl, init_job->fp8, -1);
     tc_launch_corr(init_job->ops, pa.K, B, pa.ldN, init_job->scale, init_job->rsig, nullptr, nullptr, pa.Gfull,
                    w->tc_err, st);
     k_init_tc<VT><<<(unsigned)B, 256, 0, st>>>(pa, init_job->lvl);
@@ -2242,6 +2330,9 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     k_corr<VT, CORR_INIT><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
   }
   k_init_finish<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa, o.lambda_relative);
+  // the full-dictionary check uses the same tensor-core level when the exact level is FP32 data
+  const TcJob* full_job =
+      sizeof(VT) == 4 && pa.dd.lv[pa.dd.n_levels - 1].kind == LK_F32 && pa.sp.full_gap ? init_job : nullptr;
   k_schedule<VT><<<1, 1024, 0, st>>>(pa);
   LASSO_CUDA_TRY(cudaGetLastError());
   LASSO_CUDA_TRY(cudaMemsetAsync(w->alg_bytes, 0, 16 * sizeof(double), st));
@@ -2258,7 +2349,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   double kms[6] = {0, 0, 0, 0, 0, 0};
   for (int i = 0; i < k; ++i)
     launch_pass<VT>(pa, st, has_kron, corr_grid, corr_smem, o.profile ? &evs[(size_t)i * PASS_EVENTS] : nullptr,
-                    tc_jobs, w->tc_err);
+                    tc_jobs, w->tc_err, full_job);
   cudaError_t ce = cudaStreamEndCapture(st, &graph);
   if (ce != cudaSuccess) {
     set_last_error(cudaGetErrorString(ce), __FILE__, __LINE__);
@@ -2319,7 +2410,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   double hbytes[16] = {0};
   LASSO_CUDA_TRY(cudaMemcpyAsync(hbytes, w->alg_bytes, sizeof(hbytes), cudaMemcpyDeviceToHost, st));
   LASSO_CUDA_TRY(cudaStreamSynchronize(st));
-  int64_t launches = 6 + replays * (int64_t)k * pass_launches(has_kron, pa.sp.full_gap != 0, (int)tc_jobs.size());
+  int64_t launches = 6 + replays * (int64_t)k * pass_launches(has_kron, pa.sp.full_gap != 0, (int)tc_jobs.size(), full_job != nullptr);
   {
     int herr = 0;
     LASSO_CUDA_TRY(cudaMemcpy(&herr, w->tc_err, 4, cudaMemcpyDeviceToHost));
