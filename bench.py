@@ -337,7 +337,9 @@ def run_ours(args):
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "avg_launch_us": 1e3 * kms[kind] / max(1.0, klaunch[kind]),
-                "kernel_share": {names[i]: kms[i] / max(1e-9, kms.sum()) for i in range(6) if kms[i] > 0}}
+                "kernel_share": {names[i]: kms[i] / max(1e-9, kms.sum()) for i in range(6) if kms[i] > 0},
+                "kernels_GBps": {names[i]: kbytes[i] / (kms[i] * 1e-3) / 1e9 for i in range(6)
+                                 if kms[i] > 0 and kbytes[i] > 0 and i != 5}}
     roofline["note"] = ("algorithmic bytes count every signal's own reads of its preserved atoms; the "
                         "dictionary stays in L2 across the batch, so DRAM traffic is far below them and the "
                         "HBM fraction can exceed 1 (see roofline_l2)")

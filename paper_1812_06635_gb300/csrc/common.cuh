@@ -99,6 +99,7 @@ struct SigState {
   // screening scalars of the pass: |s'|, |s'| ||rho||, test radius, |s~|, R~, 1 / lam
   double t_abs_sp, t_c_eps, t_Rs, t_abs_st, t_Rt, t_inv_lam;
   int act, scr, snap, refine;        // outcome of the pass, screen flag, snapshot, tighten request
+  int res_tight, c_res_tight;        // residual with error-free products (this pass / the snapshot)
   double best_cert;                  // exact level: best certificate so far
   int stall, pad2;                   // exact level: passes without a 2 % improvement of it
   int c_nnz, pending, next_check, pad1;
@@ -108,7 +109,7 @@ struct SigState {
 
 // e_r >= ||rho^ - (y - A~ z)|| for the residual of the current pass (see LevelDev).
 __device__ __forceinline__ double residual_bound(const LevelDev& L, double sum_kapz, int n_nz, double nrho,
-                                                 bool vt64);
+                                                 bool vt64, bool fast = false);
 
 // Knobs of a solve, as kernels see them.
 struct SolveParams {
@@ -228,8 +229,11 @@ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 namespace lasso {
 __device__ __forceinline__ double residual_bound(const LevelDev& L, double sum_kapz, int n_nz, double nrho,
-                                                 bool vt64) {
+                                                 bool vt64, bool fast) {
   const double urho = vt64 ? U64 : U32;
+  // fast: FP32 residual as plain FMA chains over the nonzeros (one chain per row), then y - acc
+  if (fast && !vt64 && L.kind != LK_KRON && !level_fp64_arith(L.kind))
+    return gamma_n((double)n_nz + 4.0, U32) * sum_kapz + 2.0 * urho * nrho;
   switch (L.res_model) {
     case RES_CHAIN:
       return gamma_n((double)n_nz + 4.0, U64) * sum_kapz + 2.0 * urho * nrho;

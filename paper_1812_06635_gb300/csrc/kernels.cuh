@@ -348,6 +348,66 @@ __device__ __forceinline__ float4 load4_f(const LevelDev& L, int64_t j, int r0) 
   return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// The same for a storage kind known at compile time (lets a loop keep several loads in flight).
+template <int KIND>
+__device__ __forceinline__ float4 load4_t(const LevelDev& L, int64_t j, int r0) {
+  if constexpr (KIND == LK_F32) {
+    return __ldg(reinterpret_cast<const float4*>((const float*)L.data + j * L.ld + r0));
+  } else if constexpr (KIND == LK_BF16) {
+    uint2 v = __ldg(reinterpret_cast<const uint2*>((const __nv_bfloat16*)L.data + j * L.ld + r0));
+    float2 a = bf16x2_to_f2(v.x), b = bf16x2_to_f2(v.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    uint32_t v = __ldg(reinterpret_cast<const unsigned int*>((const uint8_t*)L.data + j * L.ld + r0));
+    float2 a = fp8x2_to_f2((uint16_t)(v & 0xffffu)), b = fp8x2_to_f2((uint16_t)(v >> 16));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+// Residual accumulation acc[v] += sum_q w_q a~_{j_q}[r0 + v] over cnt staged nonzeros, eight
+// atom segments in flight per thread: error-free products (Dot2) when d2, plain FMA chains
+// otherwise (acc[v].s only).
+template <int KIND>
+__device__ __forceinline__ void res_accumulate(const LevelDev& L, const int32_t* s_idx, const float* s_wf, int cnt,
+                                               int r0, bool d2, DF* acc) {
+  int q = 0;
+  for (; q + 8 <= cnt; q += 8) {
+    float4 av[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) av[u] = load4_t<KIND>(L, s_idx[q + u], r0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float w = s_wf[q + u];
+      if (d2) {
+        dot2_add(acc[0], w, av[u].x);
+        dot2_add(acc[1], w, av[u].y);
+        dot2_add(acc[2], w, av[u].z);
+        dot2_add(acc[3], w, av[u].w);
+      } else {
+        acc[0].s = __fmaf_rn(w, av[u].x, acc[0].s);
+        acc[1].s = __fmaf_rn(w, av[u].y, acc[1].s);
+        acc[2].s = __fmaf_rn(w, av[u].z, acc[2].s);
+        acc[3].s = __fmaf_rn(w, av[u].w, acc[3].s);
+      }
+    }
+  }
+  for (; q < cnt; ++q) {
+    const float4 av = load4_t<KIND>(L, s_idx[q], r0);
+    const float w = s_wf[q];
+    if (d2) {
+      dot2_add(acc[0], w, av.x);
+      dot2_add(acc[1], w, av.y);
+      dot2_add(acc[2], w, av.z);
+      dot2_add(acc[3], w, av.w);
+    } else {
+      acc[0].s = __fmaf_rn(w, av.x, acc[0].s);
+      acc[1].s = __fmaf_rn(w, av.y, acc[1].s);
+      acc[2].s = __fmaf_rn(w, av.z, acc[2].s);
+      acc[3].s = __fmaf_rn(w, av.w, acc[3].s);
+    }
+  }
+}
+
 struct D4 {
   double x, y, z, w;
 };

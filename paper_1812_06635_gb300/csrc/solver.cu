@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
   __syncthreads();
   if (!s_live) return;
   const int lvl = sp->level, nnz = sp->n_nz;
+  const bool tight = sp->res_tight != 0;
   const LevelDev& L = a.dd.lv[lvl];
   const VT* y = a.Yw + (int64_t)b * a.ldN;
   VT* rho = a.Rho + (int64_t)b * a.ldN;
@@ -494,16 +495,12 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
         }
         __syncthreads();
         const int cnt = min(RES_THREADS, nnz - base);
-        if (active && L.kind == LK_F32) {
-#pragma unroll 4
-          for (int q = 0; q < cnt; ++q) {
-            const float4 av = load4_f(L, s_idx[q], r0);
-            const float w = s_wf[q];
-            dot2_add(acc[0], w, av.x);
-            dot2_add(acc[1], w, av.y);
-            dot2_add(acc[2], w, av.z);
-            dot2_add(acc[3], w, av.w);
-          }
+        if (active && (L.kind == LK_F32 || sizeof(VT) == 4)) {
+          // Dot2 once the certificate needs it, plain FMA chains before
+          const bool d2 = L.kind == LK_F32 && tight;
+          if (L.kind == LK_F32) res_accumulate<LK_F32>(L, s_idx, s_wf, cnt, r0, d2, acc);
+          else if (L.kind == LK_BF16) res_accumulate<LK_BF16>(L, s_idx, s_wf, cnt, r0, false, acc);
+          else res_accumulate<LK_FP8>(L, s_idx, s_wf, cnt, r0, false, acc);
         } else if (active) {
           for (int q = 0; q < cnt; ++q) {
             const float4 av = load4_f(L, s_idx[q], r0);
@@ -975,7 +972,7 @@ __device__ PassScalars pass_scalars(const SigState& s, const LevelDev& L, double
   PassScalars o;
   const double lam = s.lam;
   const double nrho = sqrt(rr);
-  const double e_r = residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8);
+  const double e_r = residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8, !s.res_tight);
   const double e = s.sum_epsz + e_r;
   double sp_ = 0.0, st_ = 0.0;
   if (rr > 0.0) {
@@ -1046,6 +1043,7 @@ __device__ void pass_decide(SigState& s, const PassArgs<VT>& a, double m1_bulk, 
     s.c_nnz = s.n_nz;
     s.c_m1 = m1_used;
     s.c_nrho_ru = __double2float_ru(nrho);
+    s.c_res_tight = s.res_tight;
   }
   // Dynamic Safe radius ||theta' - y/lam|| (Table I)
   const double sp_ = s.sp;
@@ -1143,6 +1141,10 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
     pass_decide<VT>(s, a, m1, m1, ps);
     check_stall<VT>(s, a, ps.cert);
   }
+  // the next residuals with error-free products once the certificate nears tol, or once the
+  // fast residual's rounding bound is a visible part of it (sticky)
+  if (!s.res_tight && s.level == I && (ps.cert <= 30.0 * a.sp.tol || ps.delta >= 0.1 * (ps.Gp + ps.delta)))
+    s.res_tight = 1;
   *sp = s;
 }
 
@@ -1669,7 +1671,7 @@ __global__ void k_full_finish(PassArgs<VT> a) {
       const double beta = yr / (lam * rr);
       sf = m1 > 0.0 ? fmin(fmax(beta, -1.0 / m1), 1.0 / m1) : beta;
     }
-    const double e = s.c_epsz + residual_bound(L, s.c_kapz, s.c_nnz, nrho, sizeof(VT) == 8);
+    const double e = s.c_epsz + residual_bound(L, s.c_kapz, s.c_nnz, nrho, sizeof(VT) == 8, !s.c_res_tight);
     const double P = 0.5 * rr + lam * s.c_l1;
     const double D = lam * sf * yr - 0.5 * lam * lam * sf * sf * rr;
     const double g = fmax(P - D + nrho * e + 0.5 * e * e, 0.0) / s.yy;
@@ -1949,7 +1951,7 @@ __global__ void k_cert_finish(PassArgs<VT> a) {
   const int nch = (int)((a.K + a.sp.chunk - 1) / a.sp.chunk);
   for (int c = 0; c < nch; ++c) m1 = fmax(m1, a.part_corr[((int64_t)b * a.nch + c) * 2]);
   const double lam = s.lam, nrho = sqrt(rr);
-  const double e = s.c_epsz + residual_bound(L, s.c_kapz, s.c_nnz, nrho, sizeof(VT) == 8);
+  const double e = s.c_epsz + residual_bound(L, s.c_kapz, s.c_nnz, nrho, sizeof(VT) == 8, !s.c_res_tight);
   double sp_ = 0.0;
   if (rr > 0.0) {
     const double beta = yr / (lam * rr);
