@@ -100,6 +100,7 @@ struct SigState {
   double t_abs_sp, t_c_eps, t_Rs, t_abs_st, t_Rt, t_inv_lam;
   int act, scr, snap, refine;        // outcome of the pass, screen flag, snapshot, tighten request
   int res_tight, c_res_tight;        // residual with error-free products (this pass / the snapshot)
+  int corr_tight, pad3;              // exact level: correlations with error-free products (sticky)
   double best_cert;                  // exact level: best certificate so far
   int stall, pad2;                   // exact level: passes without a 2 % improvement of it
   int c_nnz, pending, next_check, pad1;

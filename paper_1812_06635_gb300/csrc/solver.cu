@@ -783,7 +783,7 @@ __device__ __forceinline__ int item_signal(const int* __restrict__ offsets, int 
 // k_residual; the maxima go to the signal's state with atomicMax on FP32 bit patterns
 // (non-negative values).  Every per-atom operation is FP32; the bounds use directed rounding.
 template <typename VT>
-__global__ void __launch_bounds__(CORR_THREADS) k_corr_pass(PassArgs<VT> a) {
+__global__ void __launch_bounds__(CORR_THREADS, 4) k_corr_pass(PassArgs<VT> a) {
   static_assert(sizeof(VT) == 4, "FP32 iterates only");
   constexpr int NW = CORR_THREADS / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -804,7 +804,9 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr_pass(PassArgs<VT> a) {
     const VT* rho = a.Rho + (int64_t)b * a.ldN;
     const float nrho_f = s.nrho_ru, thr_f = s.thr_f, beta_f = s.beta_f;
     const bool from_full = L.kind == LK_KRON || L.tc;
+    const bool tight = !from_full && L.kind == LK_F32 && s.corr_tight;
     const float dq_f = L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
+    const float gt_f = tight ? __double2float_ru(L.gam_tight) : 0.f;
     const int32_t* kp = kept_of(a, b, s.parity);
     VT* X = a.X + (int64_t)b * a.K;
     VT* Z = a.Z + (int64_t)b * a.K;
@@ -812,7 +814,8 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr_pass(PassArgs<VT> a) {
     float m1 = 0.f, m2 = 0.f;
     auto update = [&](int pos, int32_t j, float g) {
       const float ag = fabsf(g);
-      float ub = __fmaf_ru(L.epsr32[j], nrho_f, __fmul_ru(ag, ga_fac));
+      const float er = tight ? __fmaf_ru(gt_f, L.kappa32[j], L.eps32[j]) : L.epsr32[j];
+      float ub = __fmaf_ru(er, nrho_f, __fmul_ru(ag, ga_fac));
       if (dq_f > 0.f) ub = __fmaf_ru(L.kappa32[j], dq_f, ub);
       m1 = fmaxf(m1, ub);
       m2 = fmaxf(m2, ag);
@@ -829,6 +832,16 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr_pass(PassArgs<VT> a) {
         const int32_t j = kp[pos];
         update(pos, j, a.Gfull[(int64_t)b * a.K + j]);
       }
+    } else if (tight) {
+      // error-free products (Dot2) with their tight bound, near the end of the signal's solve
+      for (int base = p0 + wid; base < p1; base += NW) {
+        const int32_t j = kp[base];
+        const float g = (float)warp_atom_dot(L, j, ldN, reinterpret_cast<const float*>(rho), nullptr, lane);
+        if (lane == 0) update(base, j, g);
+        if (a.alg_bytes && lane == 0)
+          bytes += (float)a.dd.N * level_elem_bytes(L.kind) + 4.f + 5.f * sizeof(VT);
+      }
+      if (a.alg_bytes && chunk == 0 && wid == 0 && lane == 0) bytes += (float)a.dd.N * sizeof(VT);
     } else {
       for (int base = p0 + wid; base < p1; base += 2 * NW) {
         const bool two = base + NW < p1;
@@ -1131,11 +1144,16 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
   s.refine = 0;
   // (with the full-dictionary stop, only a pass that may take a snapshot needs the tight value)
   const bool may_stop = !a.sp.full_gap || (!s.pending && s.iters >= s.next_check);
-  if (sizeof(VT) == 4 && L.kind == LK_F32 && s.level == I && ps.cert > a.sp.tol && rr > 0.0 && m2 > 0.0 &&
-      may_stop) {
-    // would the certificate meet tol with the tight products?  then k_screen tightens it
+  if (sizeof(VT) == 4 && L.kind == LK_F32 && !L.tc && s.level == I && ps.cert > a.sp.tol && rr > 0.0 &&
+      m2 > 0.0 && !s.corr_tight) {
+    // would the certificate meet tol with the tight products?  then the next passes compute the
+    // correlations with error-free products (sticky), and k_refine tightens this one if a
+    // snapshot may follow
     const PassScalars pe = pass_scalars<VT>(s, L, rr, yr, m2 * (1.0 + 3.0 * U32), m2);
-    if (pe.cert <= a.sp.tol) s.refine = 1;
+    if (pe.cert <= a.sp.tol) {
+      s.corr_tight = 1;
+      s.refine = may_stop ? 1 : 0;
+    }
   }
   if (!s.refine) {
     pass_decide<VT>(s, a, m1, m1, ps);
