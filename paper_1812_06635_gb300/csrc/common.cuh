@@ -121,6 +121,7 @@ struct SolveParams {
   int chunk;                // atoms per correlation work item (multiple of CORR_CHUNK)
   int full_gap;             // 1: stop on the full-dictionary gap (checked explicitly)
   int stall_passes;         // exact FP32 level: passes without progress that mark a signal saturated (0: off)
+  int corr_grid;            // blocks of the correlation pass (the per-pass chunk keeps it busy)
 };
 
 // Internal status of a signal whose FP32 iterates stopped improving on the exact level: the

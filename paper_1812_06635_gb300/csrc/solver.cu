@@ -299,21 +299,42 @@ __global__ void k_init_state(PassArgs<VT> a, const double* __restrict__ lambdas)
 
 // Prefix sum of the correlation work items of the live signals, and the done count.
 template <typename VT>
-__global__ void k_schedule(PassArgs<VT> a) {
+__global__ void k_schedule(PassArgs<VT> a, int dyn) {
   __shared__ int sh_sum[32];
   __shared__ int sh_done[32];
-  __shared__ int carry;
+  __shared__ int carry, s_chunk;
+  const int B = a.sp.B;
+  // atoms per correlation work item: the tuned chunk, halved (down to 32) while the live
+  // signals' preserved atoms would give fewer than two items per block of the pass (dyn)
+  if (dyn && sizeof(VT) == 4) {
+    long long ks = 0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x)
+      if (!a.st[b].done) ks += a.st[b].n_kept;
+    for (int m = 16; m; m >>= 1) ks += __shfl_xor_sync(0xffffffffu, ks, m);
+    if ((threadIdx.x & 31) == 0) sh_sum[threadIdx.x >> 5] = (int)min(ks, (long long)INT_MAX);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh_sum[w];
+      int ch = a.sp.chunk;
+      while (ch > CORR_CHUNK && t / ch < 2LL * a.sp.corr_grid) ch >>= 1;
+      s_chunk = ch;
+    }
+  } else if (threadIdx.x == 0) {
+    s_chunk = a.sp.chunk;
+  }
   if (threadIdx.x == 0) carry = 0;
   int done_total = 0;
   __syncthreads();
-  const int B = a.sp.B;
+  const int chunk = s_chunk;
+  if (threadIdx.x == 0) a.counters[2] = chunk;
   for (int base = 0; base < B; base += blockDim.x) {
     int b = base + threadIdx.x;
     int items = 0, dn = 0;
     if (b < B) {
       const SigState& s = a.st[b];
       dn = s.done;
-      items = s.done ? 0 : s.n_chunks;
+      items = s.done ? 0 : (s.n_kept + chunk - 1) / chunk;
     }
     // block exclusive scan of items
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -790,7 +811,7 @@ __global__ void __launch_bounds__(CORR_THREADS, 4) k_corr_pass(PassArgs<VT> a) {
   const int B = a.sp.B;
   const int total = a.offsets[B];
   const int ldN = (int)a.ldN;
-  const int CH = a.sp.chunk;
+  const int CH = a.counters[2];      // this pass's chunk (k_schedule)
   const float ga_fac = 1.0000004f;   // >= 1 + 3 u32, rounded up
   const float inv_Lf = (float)a.sp.inv_L;
   const bool fista = a.sp.algo == LASSO_FISTA;
@@ -2144,7 +2165,7 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
     k_full_finish<VT><<<B, 128, 0, st>>>(pa);
   }
   if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
-  k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+  k_schedule<VT><<<1, 1024, 0, st>>>(pa, 1);
   if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
 }
 
@@ -2206,7 +2227,7 @@ static int tune_corr(lasso_dict* d, const PassArgs<VT>& pa0, int64_t B, cudaStre
   for (int c : chunks) {
     pa.sp.chunk = c;
     k_tune_state<VT><<<(unsigned)B, 256, 0, st>>>(pa, n_kept);
-    k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+    k_schedule<VT><<<1, 1024, 0, st>>>(pa, 0);
     for (int g : grids) {
       const int grid = num_sms() * g;
       k_corr_pass<VT><<<grid, CORR_THREADS, 0, st>>>(pa);   // warm-up
@@ -2335,7 +2356,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   const int corr_grid = num_sms() * corr_bps;
   // init: lambda_max and a^T y bounds with the most precise level
   LASSO_CUDA_TRY(cudaMemsetAsync(w->tc_err, 0, 4, st));
-  k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+  k_schedule<VT><<<1, 1024, 0, st>>>(pa, 0);
   // initial pass: on the tensor cores when a BF16 (else FP8) level runs there, else exact products
   const TcJob* init_job = nullptr;
   for (const TcJob& j : tc_jobs)
@@ -2350,10 +2371,11 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     k_corr<VT, CORR_INIT><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
   }
   k_init_finish<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa, o.lambda_relative);
+  pa.sp.corr_grid = corr_grid;
   // the full-dictionary check uses the same tensor-core level when the exact level is FP32 data
   const TcJob* full_job =
       sizeof(VT) == 4 && pa.dd.lv[pa.dd.n_levels - 1].kind == LK_F32 && pa.sp.full_gap ? init_job : nullptr;
-  k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+  k_schedule<VT><<<1, 1024, 0, st>>>(pa, 1);
   LASSO_CUDA_TRY(cudaGetLastError());
   LASSO_CUDA_TRY(cudaMemsetAsync(w->alg_bytes, 0, 16 * sizeof(double), st));
   // capture k passes
@@ -2770,7 +2792,7 @@ static int run_lambda_max(lasso_dict* d, Workspace* w, const float* Y, int64_t B
   trace_step(st, "lmax: k_load_y");
   k_init_state<VT><<<(unsigned)B, 256, 0, st>>>(pa, nullptr);
   trace_step(st, "lmax: k_init_state");
-  k_schedule<VT><<<1, 1024, 0, st>>>(pa);
+  k_schedule<VT><<<1, 1024, 0, st>>>(pa, 0);
   trace_step(st, "lmax: k_schedule");
   k_corr<VT, CORR_INIT><<<num_sms() * 8, CORR_THREADS, 0, st>>>(pa);
   trace_step(st, "lmax: k_corr init");
