@@ -130,6 +130,29 @@ __device__ __forceinline__ double warp_atom_dot(const LevelDev& L, int64_t j, in
   return 0.0;
 }
 
+// Dot2 (error-free products, TwoSum accumulation) of atom row j of an FP32 level with rho, all in
+// FP32: the double-float result s + c is rounded once to FP32 (within 3 u |g|, which the bound
+// of the caller covers); the same value in every lane.
+__device__ __forceinline__ float warp_atom_dot_tight_f(const LevelDev& L, int64_t j, int ldN,
+                                                      const float* __restrict__ rho_f, int lane) {
+  const float4* row = reinterpret_cast<const float4*>((const float*)L.data + j * L.ld);
+  const float4* rs = reinterpret_cast<const float4*>(rho_f);
+  DF acc;
+  acc.init();
+  const int nv = ldN >> 2;
+#pragma unroll 4
+  for (int k = lane; k < nv; k += 32) {
+    const float4 a = __ldg(row + k);
+    const float4 r = __ldg(rs + k);
+    dot2_add(acc, a.x, r.x);
+    dot2_add(acc, a.y, r.y);
+    dot2_add(acc, a.z, r.z);
+    dot2_add(acc, a.w, r.w);
+  }
+  acc = df_warp_reduce(acc);
+  return __fadd_rn(acc.s, acc.c);
+}
+
 // Fast warp dot product for the bulk of a pass: plain FMA chains (two independent FP32 or FP64
 // accumulators per lane), rho read through L1 straight from global memory.  The rounding error
 // is bounded by gamma_{ld/32 + 8} sum_i |a_i rho_i| (the LevelDev's gam_corr), which the stable

@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(CORR_THREADS, 4) k_corr_pass(PassArgs<VT> a) {
       // error-free products (Dot2) with their tight bound, near the end of the signal's solve
       for (int base = p0 + wid; base < p1; base += NW) {
         const int32_t j = kp[base];
-        const float g = (float)warp_atom_dot(L, j, ldN, reinterpret_cast<const float*>(rho), nullptr, lane);
+        const float g = warp_atom_dot_tight_f(L, j, ldN, reinterpret_cast<const float*>(rho), lane);
         if (lane == 0) update(base, j, g);
         if (a.alg_bytes && lane == 0)
           bytes += (float)a.dd.N * level_elem_bytes(L.kind) + 4.f + 5.f * sizeof(VT);
