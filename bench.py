@@ -41,6 +41,8 @@ def _args():
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--grid", action="store_true",
+                    help="run the Section V parameter grid instead (T/T_N, F/F_N per point)")
     return ap.parse_args()
 
 
@@ -398,10 +400,88 @@ def run_ours(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- Section V grid
+
+def run_grid(args):
+    """The experiments' parameter pool (Section V) on synthetic inputs of their size (N = 2500,
+    K = 10000, unit-norm y, x Bernoulli(0.02)-Gaussian, 25 realisations solved as one batch):
+    lambda / lambda_max log-spaced in [1e-2, 1], tol in {1e-3, 1e-6}, FISTA / ISTA, GAP / Dynamic Safe,
+    Gamma in {0.01, 0.1, 0.8}; fast dictionaries: the FP8 -> BF16 precision ladder of a Gaussian A, and
+    Kronecker truncations (R = 1, 2 of 4 terms) of structured dictionaries with term decay 0.3 / 0.5 / 0.7.
+    Each line reports T / T_N, the batch time over that of the same engine without screening on the
+    exact dictionary (the paper's normalisation), and F / F_N, the atom work weighted by each level's
+    relative complexity over that of the unscreened exact solve.  One JSON line per grid point."""
+    import torch
+    import synthetic as S
+    import paper_1812_06635_gb300 as pkg
+    from paper_1812_06635_gb300 import build
+    build.build()
+    pkg.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ratios_grid = [0.01, 0.03, 0.1, 0.3, 0.7]
+    NO_SCREEN = 1 << 30
+
+    def timed(d, Y, lam, tol, **kw):
+        d.solve_batch(Y, lam, tol, **kw)                     # warm (tuning, workspace)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, gaps, status, iters, st = d.solve_batch(Y, lam, tol, **kw)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, st, int(((status == 0) & (gaps <= tol)).sum())
+
+    def work(st, rc):
+        return sum(st.level_atoms[i] * rc[i] for i in range(len(rc)))
+
+    def point(family, d, d_exact, rc, Y, lmax, ratio, tol, algo=0, rule=0, Gamma=0.5):
+        lam = torch.full((Y.shape[0],), ratio, dtype=torch.float64, device=dev) * lmax
+        T, st, ok = timed(d, Y, lam, tol, algo=algo, rule=rule, Gamma=Gamma)
+        TN, stn, okn = timed(d_exact, Y, lam, tol, algo=algo, rule=rule, screen_every=NO_SCREEN)
+        F, FN = work(st, rc), float(d_exact.K) * sum(stn.level_passes)
+        line = {"grid": {"dictionary": family, "lambda_ratio": ratio, "tol": tol, "algo": ["FISTA", "ISTA"][algo],
+                         "rule": ["GAP", "DST", "STATIC"][rule], "Gamma": Gamma, "signals": int(Y.shape[0])},
+                "T_ms": 1e3 * T, "T_N_ms": 1e3 * TN, "T/T_N": T / TN, "F/F_N": F / max(FN, 1.0),
+                "solved": ok, "solved_N": okn, "passes_max": st.passes, "passes_max_N": stn.passes,
+                "level_passes_per_signal": [v / Y.shape[0] for v in st.level_passes[:len(rc)]]}
+        print(json.dumps(line), flush=True)
+
+    # Gaussian dictionary with the precision ladder
+    w = S.paper_dense(n_signals=25)
+    Y = torch.tensor(w.Y, dtype=torch.float32, device=dev)
+    d = pkg.Dictionary.dense(w.A, dtype="f32").add_level(pkg.LEVEL_FP8).add_level(pkg.LEVEL_BF16).prepare()
+    d_exact = pkg.Dictionary.dense(w.A, dtype="f32").prepare()
+    rc = d.info()["rc"]
+    lmax = d.lambda_max(Y)
+    for tol in (1e-3, 1e-6):
+        for ratio in ratios_grid:
+            point("gaussian+fp8/bf16", d, d_exact, rc, Y, lmax, ratio, tol)
+    for G in (0.01, 0.1, 0.8):
+        point("gaussian+fp8/bf16", d, d_exact, rc, Y, lmax, 0.1, 1e-6, Gamma=G)
+    point("gaussian+fp8/bf16", d, d_exact, rc, Y, lmax, 0.1, 1e-6, algo=1)
+    point("gaussian+fp8/bf16", d, d_exact, rc, Y, lmax, 0.1, 1e-6, rule=1)
+    d.close()
+    d_exact.close()
+    # structured dictionaries: three error profiles
+    for decay in (0.3, 0.5, 0.7):
+        wk = S.paper_kron(decay, n_signals=25)
+        Yk = torch.tensor(wk.Y, dtype=torch.float32, device=dev)
+        dk = pkg.Dictionary.kron(wk.Bf, wk.Cf).add_level(pkg.LEVEL_KRON, 1).add_level(pkg.LEVEL_KRON, 2).prepare()
+        dkx = pkg.Dictionary.kron(wk.Bf, wk.Cf).prepare()
+        rck = dk.info()["rc"]
+        lm = dk.lambda_max(Yk)
+        for ratio in ratios_grid:
+            point(f"kron-decay{decay}", dk, dkx, rck, Yk, lm, ratio, 1e-6)
+        dk.close()
+        dkx.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.grid:
+        return run_grid(args)
     return run_ours(args)
 
 

@@ -34,9 +34,11 @@ __all__ = [
     "DenseWorkload", "KronWorkload", "rng_for",
     "gaussian_unit_columns", "bernoulli_gaussian",
     "c1", "c2", "c3", "c4", "c5", "dense_small", "kron_small", "orthonormal_case",
+    "paper_dense", "paper_kron",
 ]
 
-_CFG = {"c1": 1, "c2": 2, "c3": 3, "c4": 4, "c5": 5, "dense_small": 6, "kron_small": 7, "ortho": 8}
+_CFG = {"c1": 1, "c2": 2, "c3": 3, "c4": 4, "c5": 5, "dense_small": 6, "kron_small": 7, "ortho": 8,
+        "paper_dense": 9, "paper_kron": 10}
 _DICT, _SIGNAL = 0, 1
 
 
@@ -254,3 +256,27 @@ def kron_small(R: int = 3, N1: int = 4, K1: int = 6, N2: int = 5, K2: int = 7, n
     Bf, Cf = _kron_factors("kron_small", R, N1, K1, N2, K2, seed, decay)
     Y, ratios, sups, cfs = _kron_signals("kron_small", Bf, Cf, n_signals, seed, p, ratio, False)
     return KronWorkload("kron_small", Bf, Cf, Y, ratios, 1e-6, sups, cfs)
+
+
+# ----------------------------------------------------------------------------- Section V setting
+
+def _unit_rows(Y):
+    n = np.linalg.norm(Y, axis=1, keepdims=True)
+    return Y / np.where(n > 0, n, 1.0)
+
+
+def paper_dense(n_signals: int = 25, seed: int = 0, N: int = 2500, K: int = 10000) -> DenseWorkload:
+    """The experiments' setting (Section V) with a Gaussian dictionary: N = 2500, K = 10000, unit-norm
+    y = A x with x Bernoulli(0.02)-Gaussian, 25 realisations; lambda ratios are chosen by the caller."""
+    A, Y, ratios, sups, cfs, _ = _dense_batch("paper_dense", N, K, n_signals, seed, 0.02, None, False,
+                                              fixed_ratio=1.0)
+    return DenseWorkload("paper_dense", A, _f32(_unit_rows(Y)), ratios, 1e-6, sups, cfs)
+
+
+def paper_kron(decay: float, n_signals: int = 25, seed: int = 0) -> KronWorkload:
+    """The experiments' setting with a structured dictionary: A = (sum_{r<4} w_r B_r (x) C_r) diag(d),
+    B_r, C_r 50 x 100 (N = 2500, K = 10000), term weights w_r = decay^r (small decay: well approximated
+    by few terms, the paper's easy scenario; large decay: hard), unit-norm y = A x, x Bernoulli(0.02)."""
+    Bf, Cf = _kron_factors("paper_kron", 4, 50, 100, 50, 100, seed, decay)
+    Y, ratios, sups, cfs = _kron_signals("paper_kron", Bf, Cf, n_signals, seed, 0.02, None, False, fixed_ratio=1.0)
+    return KronWorkload(f"paper_kron-decay{decay}", Bf, Cf, _f32(_unit_rows(Y)), ratios, 1e-6, sups, cfs)
