@@ -6,6 +6,8 @@ Test infrastructure only (see the package docstring).
 * ``KronDict``   A~ = (sum_{r<=R} B_r (x) C_r) diag(d) evaluated with small matrix products
                  (the SuKro structure of Section V-A), row-major vectorisation
                  (B (x) C)[n1 N2 + n2, k1 K2 + k2] = B[n1, k1] C[n2, k2].
+* ``FaustDict``  A~ = S_0 S_1 ... S_{J-1}, a product of sparse factors (the FAuST structure of
+                 Section VI), applied factor by factor.
 * quantisers     BF16 (round to nearest even) and FP8 E4M3 with a per-atom scale
                  s_j = max_i |a_ij| / 448, written from the formats' definitions.
 * ``Level``      one rung of the ladder {A~^i} with eps^i_j >= ||a~^i_j - a_j||_2 and RC_i
@@ -102,6 +104,82 @@ class KronDict:
 
     def atom_norms(self):
         return np.array([np.linalg.norm(self.col(j)) for j in range(self.K)])
+
+
+class FaustDict:
+    """A~ = S_0 S_1 ... S_{J-1} with S_f sparse (CSR: row pointers, column indices, values).
+
+    matvec:  A~ x = S_0 (S_1 (... (S_{J-1} x)))
+    rmatvec: A~^T rho = S_{J-1}^T (... (S_0^T rho))
+    Each factor product is the plain definition (out_i = sum_p v_p in_{c_p} over row i), written
+    with ``np.bincount`` in FP64.  Restricted products evaluate every atom and select.
+    """
+
+    def __init__(self, factors):
+        self.f = []
+        for S in factors:
+            indptr = np.asarray(S.indptr, np.int64)
+            rows, cols = S.shape
+            row_of = np.repeat(np.arange(rows), np.diff(indptr))
+            self.f.append((rows, cols, row_of, np.asarray(S.indices, np.int64), np.asarray(S.data, np.float64)))
+        self.N = self.f[0][0]
+        self.K = self.f[-1][1]
+        for (r0, c0, *_), (r1, c1, *_) in zip(self.f[:-1], self.f[1:]):
+            assert c0 == r1, "inner dimensions of consecutive factors must agree"
+
+    @staticmethod
+    def _apply(fac, v):
+        rows, cols, row_of, col, val = fac
+        return np.bincount(row_of, weights=val * v[col], minlength=rows)
+
+    @staticmethod
+    def _apply_t(fac, v):
+        rows, cols, row_of, col, val = fac
+        return np.bincount(col, weights=val * v[row_of], minlength=cols)
+
+    def matvec(self, x, idx=None):
+        v = np.zeros(self.K)
+        if idx is None:
+            v[:] = x
+        else:
+            v[idx] = x
+        for fac in reversed(self.f):
+            v = self._apply(fac, v)
+        return v
+
+    def rmatvec(self, rho, idx=None):
+        v = np.asarray(rho, dtype=np.float64)
+        for fac in self.f:
+            v = self._apply_t(fac, v)
+        return v if idx is None else v[idx]
+
+    def col(self, j):
+        e = np.zeros(self.K)
+        e[int(j)] = 1.0
+        return self.matvec(e)
+
+    def dense(self):
+        M = np.eye(self.K)
+        for fac in reversed(self.f):
+            rows, cols, row_of, col, val = fac
+            out = np.zeros((rows, M.shape[1]))
+            np.add.at(out, row_of, val[:, None] * M[col])
+            M = out
+        return M
+
+    def abs_dense(self):
+        """|S_0| |S_1| ... |S_{J-1}| (entrywise absolute values of the factors), explicit."""
+        op = FaustDict.__new__(FaustDict)
+        op.f = [(r, c, ro, co, np.abs(v)) for (r, c, ro, co, v) in self.f]
+        op.N, op.K = self.N, self.K
+        return op.dense()
+
+    def nnz(self):
+        return int(sum(fac[4].size for fac in self.f))
+
+    def atom_norms(self):
+        M = self.dense()
+        return np.sqrt(np.einsum("nk,nk->k", M, M))
 
 
 def kron_unit_scale(Bf, Cf, R=None) -> np.ndarray:
@@ -227,6 +305,18 @@ def kron_level(Bf, Cf, d, R_keep, exact_dense=None, rc=None) -> Level:
                   np.einsum("rnk,snk->rsk", op.Bf[:R_keep], op.Bf[:R_keep]),
                   np.einsum("rnk,snk->rsk", op.Cf[:R_keep], op.Cf[:R_keep])).reshape(-1), 0.0)) * d
     return Level(f"kron{R_keep}", op, eps, rc, atn)
+
+
+def faust_level(factors, exact_dense: np.ndarray, rc=None, name="faust") -> Level:
+    """Product of sparse factors as a ladder level: eps_j = ||a~_j - a_j|| from the explicit FP64
+    product, RC defaulting to the nonzeros of the factors over N K (one multiply-add per nonzero
+    against N K for the dense product)."""
+    op = FaustDict(factors)
+    Ad = op.dense()
+    eps = exact_errors(Ad, exact_dense)
+    if rc is None:
+        rc = op.nnz() / (op.N * op.K)
+    return Level(name, op, eps, rc, np.sqrt(np.einsum("nk,nk->k", Ad, Ad)))
 
 
 def power_iteration_sq_norm(op, iters: int = 200, safety: float = 1.001) -> float:

@@ -34,11 +34,11 @@ __all__ = [
     "DenseWorkload", "KronWorkload", "rng_for",
     "gaussian_unit_columns", "bernoulli_gaussian",
     "c1", "c2", "c3", "c4", "c5", "dense_small", "kron_small", "orthonormal_case",
-    "paper_dense", "paper_kron",
+    "paper_dense", "paper_kron", "FaustWorkload", "meg_faust", "faust_small",
 ]
 
 _CFG = {"c1": 1, "c2": 2, "c3": 3, "c4": 4, "c5": 5, "dense_small": 6, "kron_small": 7, "ortho": 8,
-        "paper_dense": 9, "paper_kron": 10}
+        "paper_dense": 9, "paper_kron": 10, "meg_faust": 11, "faust_small": 12}
 _DICT, _SIGNAL = 0, 1
 
 
@@ -280,3 +280,118 @@ def paper_kron(decay: float, n_signals: int = 25, seed: int = 0) -> KronWorkload
     Bf, Cf = _kron_factors("paper_kron", 4, 50, 100, 50, 100, seed, decay)
     Y, ratios, sups, cfs = _kron_signals("paper_kron", Bf, Cf, n_signals, seed, 0.02, None, False, fixed_ratio=1.0)
     return KronWorkload(f"paper_kron-decay{decay}", Bf, Cf, _f32(_unit_rows(Y)), ratios, 1e-6, sups, cfs)
+
+
+# ----------------------------------------------------------------------------- sparse-factor products
+
+@dataclass
+class FaustWorkload:
+    """A dense dictionary with a ladder of products of sparse factors approximating it.
+
+    ``levels[i]`` is a list of J scipy CSR matrices S_0 (N x n_1), ..., S_{J-1} (n_{J-1} x K) whose
+    product approximates ``A`` column by column (the column scale of ``A`` is already folded into
+    the last factor).  Factor values and ``A`` are FP32 values held in float64.
+    """
+    name: str
+    A: np.ndarray                 # N x K exact dictionary (unit columns up to FP32 rounding)
+    levels: list                  # coarsest first
+    Y: np.ndarray
+    lam_ratio: np.ndarray
+    tol: float
+    supports: list = field(default_factory=list)
+    coefs: list = field(default_factory=list)
+
+    @property
+    def N(self):
+        return self.A.shape[0]
+
+    @property
+    def K(self):
+        return self.A.shape[1]
+
+
+def _ranked_rows(rows: int, cols: int, per_row: int, decay: float, rng: np.random.Generator):
+    """Column indices (distinct within a row) and values of a row-sparse matrix whose r-th entry of
+    every row has scale decay^r, so that keeping the first m entries of each row keeps the largest."""
+    ci = np.stack([rng.choice(cols, per_row, replace=False) for _ in range(rows)])
+    v = rng.standard_normal((rows, per_row)) * (decay ** np.arange(per_row))[None, :]
+    return ci, v
+
+
+def _csr(rows: int, cols: int, r_idx, c_idx, vals):
+    """Canonical CSR matrix (column indices sorted within each row, int32) from triplets, built with
+    an explicit lexicographic sort so that no in-place index sorting is relied on."""
+    import scipy.sparse as sps
+    r_idx = np.asarray(r_idx, np.int64)
+    c_idx = np.asarray(c_idx, np.int64)
+    order = np.lexsort((c_idx, r_idx))
+    indptr = np.zeros(rows + 1, np.int64)
+    np.cumsum(np.bincount(r_idx, minlength=rows), out=indptr[1:])
+    return sps.csr_matrix((np.asarray(vals, np.float64)[order].copy(), c_idx[order].astype(np.int32),
+                           indptr.astype(np.int32)), shape=(rows, cols))
+
+
+def _csr_first(ci: np.ndarray, v: np.ndarray, m: int, cols: int, col_scale=None, transpose=False):
+    """CSR matrix of the first m entries of every row (FP32 values); optionally transposed (for
+    factors drawn column by column) and scaled per column of the result."""
+    rows = ci.shape[0]
+    r_idx = np.repeat(np.arange(rows), m)
+    c_idx = ci[:, :m].reshape(-1)
+    vals = v[:, :m].reshape(-1)
+    if transpose:
+        rows, cols, r_idx, c_idx = cols, rows, c_idx, r_idx
+    if col_scale is not None:
+        vals = vals * np.asarray(col_scale)[c_idx]
+    return _csr(rows, cols, r_idx, c_idx, _f32(vals))
+
+
+def _faust_problem(name, N, K, n_signals, seed, first, decay, sigma, per_row, per_col, levels, n_active,
+                   ratio, unit_y):
+    """A = normalise(S_0 S_1 S_2 + E): S_0, S_1 N x N with `per_row` entries per row, S_2 N x K with
+    `per_col` entries per column (entry scales decaying with rank), E dense Gaussian with relative
+    column norm `sigma` (the part no sparse product captures).  Level (m0, m2) keeps the first m0
+    entries of each row of S_0, S_1 and the first m2 of each column of S_2, scaled by the same d."""
+    r = rng_for(seed, name, _DICT)
+    c0, v0 = _ranked_rows(N, N, per_row, decay, r)
+    c1, v1 = _ranked_rows(N, N, per_row, decay, r)
+    c2, v2 = _ranked_rows(K, N, per_col, decay, r)
+    full = [_csr_first(c0, v0, per_row, N), _csr_first(c1, v1, per_row, N),
+            _csr_first(c2, v2, per_col, N, transpose=True)]
+    P = (full[0] @ (full[1] @ full[2].toarray()))
+    E = r.standard_normal((N, K)) * (np.linalg.norm(P, axis=0) / np.sqrt(N))[None, :] * sigma
+    A_raw = P + E
+    d = 1.0 / np.linalg.norm(A_raw, axis=0)
+    A = _f32(A_raw * d[None, :])
+    ladder = [[_csr_first(c0, v0, m0, N), _csr_first(c1, v1, m0, N),
+               _csr_first(c2, v2, m2, N, col_scale=d, transpose=True)] for (m0, m2) in levels]
+    Y = np.empty((n_signals, N))
+    sups, cfs = [], []
+    for b in range(n_signals):
+        rs = rng_for(seed, name, _SIGNAL, first + b)
+        idx = np.sort(rs.choice(K, n_active, replace=False))
+        vals = rs.standard_normal(n_active)
+        Y[b] = A[:, idx] @ vals
+        sups.append(idx)
+        cfs.append(vals)
+    if unit_y:
+        Y = _unit_rows(Y)
+    return A, ladder, _f32(Y), np.full(n_signals, ratio), sups, cfs
+
+
+def meg_faust(n_signals: int = 50, seed: int = 0, first: int = 0, N: int = 204, K: int = 8193,
+              decay: float = 0.45, sigma: float = 0.055, levels=((3, 4), (4, 5), (5, 7), (6, 8))) -> FaustWorkload:
+    """Stand-in for the source-localisation experiment of Section VI: a 204 x 8193 operator with four
+    sparse-factor approximations of decreasing error (mean eps_j from about 0.2 down to the 0.055
+    floor of the dense part), 8 active sources with N(0, 1) weights, y = A x unit-norm,
+    lambda = 0.1 lambda_max, 50 runs."""
+    A, ladder, Y, ratios, sups, cfs = _faust_problem("meg_faust", N, K, n_signals, seed, first, decay, sigma, 12, 16,
+                                                    levels, 8, 0.1, True)
+    return FaustWorkload("meg_faust", A, ladder, Y, ratios, 1e-6, sups, cfs)
+
+
+def faust_small(N: int = 48, K: int = 160, n_signals: int = 4, seed: int = 0, decay: float = 0.45,
+                sigma: float = 0.05, levels=((2, 2), (3, 4)), n_active: int = 4, ratio: float = 0.2) -> FaustWorkload:
+    """Small sparse-factor problem for parity tests (sizes chosen by the caller)."""
+    A, ladder, Y, ratios, sups, cfs = _faust_problem("faust_small", N, K, n_signals, seed, 0, decay, sigma, 6, 6,
+                                                    levels, n_active, ratio, True)
+    return FaustWorkload("faust_small", A, ladder, Y, ratios, 1e-6, sups, cfs)

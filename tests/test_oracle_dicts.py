@@ -79,6 +79,71 @@ def test_kron_truncation_eps_gram_equals_column_differences():
         np.testing.assert_allclose(lev.atnorm, np.linalg.norm(trunc, axis=0), rtol=1e-10)
 
 
+def _dense_factors(factors):
+    return [np.asarray(f.toarray(), np.float64) for f in factors]
+
+
+@pytest.mark.parametrize("dims", [(7, 11), (6, 9, 13), (5, 8, 4, 12)])
+def test_faust_operator_against_explicit_product(dims):
+    """S_0 ... S_{J-1} applied factor by factor equals the explicit product of the dense factors
+    (rectangular shapes, J = 1, 2, 3), adjoint included; restricted products select atoms."""
+    r = np.random.default_rng(len(dims))
+    facs = []
+    for a, b in zip(dims[:-1], dims[1:]):
+        M = r.standard_normal((a, b)) * (r.random((a, b)) < 0.4)
+        rr, cc = np.nonzero(M)
+        facs.append(S.gen._csr(a, b, rr, cc, M[rr, cc]))
+    Ds = _dense_factors(facs)
+    M = Ds[0] if len(Ds) == 1 else np.linalg.multi_dot(Ds)
+    op = D.FaustDict(facs)
+    assert (op.N, op.K) == M.shape
+    x, rho = r.standard_normal(op.K), r.standard_normal(op.N)
+    np.testing.assert_allclose(op.matvec(x), M @ x, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(op.rmatvec(rho), M.T @ rho, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(op.dense(), M, rtol=0, atol=1e-13)
+    assert abs(float(op.matvec(x) @ rho) - float(x @ op.rmatvec(rho))) <= 1e-12 * (1 + abs(float(x @ op.rmatvec(rho))))
+    absM = np.abs(Ds[0]) if len(Ds) == 1 else np.linalg.multi_dot([np.abs(F) for F in Ds])
+    np.testing.assert_allclose(op.abs_dense(), absM, rtol=0, atol=1e-13)
+    idx = np.array([0, 3, op.K - 1])
+    np.testing.assert_allclose(op.matvec(x[idx], idx), M[:, idx] @ x[idx], atol=1e-13)
+    np.testing.assert_allclose(op.rmatvec(rho, idx), M[:, idx].T @ rho, atol=1e-13)
+    for j in idx:
+        np.testing.assert_allclose(op.col(j), M[:, j], atol=1e-14)
+
+
+def test_faust_level_errors_and_exact_product():
+    """eps_j of a sparse-factor level is the column distance to the exact atoms; it vanishes when the
+    exact dictionary is the product itself; RC counts the factors' nonzeros over N K."""
+    w = S.faust_small(N=24, K=40, levels=((2, 2), (3, 3), (6, 6)))
+    for facs in w.levels:
+        P = np.linalg.multi_dot(_dense_factors(facs))
+        lev = D.faust_level(facs, w.A)
+        np.testing.assert_allclose(lev.eps, np.linalg.norm(P - w.A, axis=0), rtol=1e-10, atol=1e-15)
+        np.testing.assert_allclose(lev.atnorm, np.linalg.norm(P, axis=0), rtol=1e-12)
+        assert lev.rc == pytest.approx(sum(f.nnz for f in facs) / (24 * 40))
+        self_lev = D.faust_level(facs, P)
+        assert np.all(self_lev.eps <= 1e-13)
+    # keeping more entries of each factor brings the product closer to A
+    means = [float(D.faust_level(f, w.A).eps.mean()) for f in w.levels]
+    assert means[0] > means[1] > means[2]
+
+
+def test_generator_faust_ladder_matches_section_vi_profile():
+    """The source-localisation stand-in: 204 x 8193, unit atoms, four levels with mean eps_j
+    decreasing from about 0.2 to about 0.06 (the profile of the paper's FAuST approximations)."""
+    w = S.meg_faust(n_signals=3)
+    assert w.A.shape == (204, 8193)
+    np.testing.assert_allclose(np.linalg.norm(w.A, axis=0), 1.0, atol=1e-6)
+    means = []
+    for facs in w.levels:
+        assert facs[0].shape == (204, 204) and facs[1].shape == (204, 204) and facs[2].shape == (204, 8193)
+        means.append(float(D.faust_level(facs, w.A).eps.mean()))
+    assert all(a > b for a, b in zip(means, means[1:]))
+    assert 0.15 < means[0] < 0.3 and 0.045 < means[-1] < 0.075
+    np.testing.assert_allclose(np.linalg.norm(w.Y, axis=1), 1.0, rtol=1e-6)
+    assert all(len(s) == 8 for s in w.supports) and np.all(w.lam_ratio == 0.1)
+
+
 def test_generator_kron_norms_agree_with_oracle():
     w = S.kron_small(R=3, N1=4, K1=6, N2=5, K2=7, n_signals=1)
     np.testing.assert_allclose(1.0 / S.gen.kron_column_norms(w.Bf, w.Cf), D.kron_unit_scale(w.Bf, w.Cf),

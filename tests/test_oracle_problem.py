@@ -306,6 +306,24 @@ def test_fast_l1_kronecker_ladder():
         assert np.linalg.norm(r.x - xs) <= 1e-5 * max(np.linalg.norm(xs), 1e-30)
 
 
+def test_fast_l1_sparse_factor_ladder():
+    """Products of sparse factors (Section VI) of increasing density, then the exact dense A: the
+    rejections are safe and the exact minimiser is reached."""
+    w = S.faust_small(N=40, K=120, n_signals=3, levels=((2, 2), (3, 4)), ratio=0.15)
+    levels = [D.faust_level(f, w.A, name=f"faust{i}") for i, f in enumerate(w.levels)] + [D.exact_level(w.A)]
+    for b in range(3):
+        y = w.Y[b]
+        lam = w.lam_ratio[b] * L.lambda_max(w.A.T @ y)
+        xs, ts = _theta_star(w.A, y, lam)
+        r = SV.fast_l1(levels, levels[-1].atnorm, y, lam, 1e-13, Gamma=0.5, trace=True, max_iter=100000)
+        assert r.converged
+        for _, rej in r.rejected_trace:
+            assert np.all(xs[rej] == 0.0)
+            assert np.all(np.abs(w.A.T @ ts)[rej] < 1.0)
+        assert all(a <= b for a, b in zip(r.level_trace, r.level_trace[1:]))
+        assert np.linalg.norm(r.x - xs) <= 1e-5 * max(np.linalg.norm(xs), 1e-30)
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_structured_polish_matches_brute_force(seed):
     """The operator form of the KKT polish (support columns formed from the Kronecker factors,
