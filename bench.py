@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--grid", action="store_true",
                     help="run the Section V parameter grid instead (T/T_N, F/F_N per point)")
+    ap.add_argument("--grid-families", default="gaussian,kron,faust",
+                    help="comma list of grid families: gaussian, kron, faust")
     return ap.parse_args()
 
 
@@ -331,7 +333,7 @@ def run_ours(args):
     # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
     hbm, bf16, peak_src = _peaks()
     kind = int(np.argmax(kms))
-    names = ["k_residual", "k_corr", "k_screen", "k_schedule", "k_kron_gemm", "k_tc_gemm"]
+    names = ["k_residual", "k_corr", "k_screen", "k_schedule", "k_structured", "k_tc_gemm"]
     achieved = kbytes[kind] / (kms[kind] * 1e-3) / 1e9 if kms[kind] > 0 else 0.0
     per_launch_bytes = kbytes[kind] / max(1.0, klaunch[kind])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -407,8 +409,10 @@ def run_grid(args):
     K = 10000, unit-norm y, x Bernoulli(0.02)-Gaussian, 25 realisations solved as one batch):
     lambda / lambda_max log-spaced in [1e-2, 1], tol in {1e-3, 1e-6}, FISTA / ISTA, GAP / Dynamic Safe,
     Gamma in {0.01, 0.1, 0.8}; fast dictionaries: the FP8 -> BF16 precision ladder of a Gaussian A, and
-    Kronecker truncations (R = 1, 2 of 4 terms) of structured dictionaries with term decay 0.3 / 0.5 / 0.7.
-    Each line reports T / T_N, the batch time over that of the same engine without screening on the
+    Kronecker truncations (R = 1, 2 of 4 terms) of structured dictionaries with term decay 0.3 / 0.5 / 0.7;
+    and the source-localisation setting of Section VI on its synthetic stand-in (204 x 8193, 50 signals
+    of 8 active sources, lambda = 0.1 lambda_max) with four sparse-factor product levels, or only the
+    finest one.  Each line reports T / T_N, the batch time over that of the same engine without screening on the
     exact dictionary (the paper's normalisation), and F / F_N, the atom work weighted by each level's
     relative complexity over that of the unscreened exact solve.  One JSON line per grid point."""
     import torch
@@ -433,7 +437,7 @@ def run_grid(args):
     def work(st, rc):
         return sum(st.level_atoms[i] * rc[i] for i in range(len(rc)))
 
-    def point(family, d, d_exact, rc, Y, lmax, ratio, tol, algo=0, rule=0, Gamma=0.5):
+    def point(family, d, d_exact, rc, Y, lmax, ratio, tol, algo=0, rule=0, Gamma=0.5, screened_exact=False):
         lam = torch.full((Y.shape[0],), ratio, dtype=torch.float64, device=dev) * lmax
         T, st, ok = timed(d, Y, lam, tol, algo=algo, rule=rule, Gamma=Gamma)
         TN, stn, okn = timed(d_exact, Y, lam, tol, algo=algo, rule=rule, screen_every=NO_SCREEN)
@@ -443,8 +447,36 @@ def run_grid(args):
                 "T_ms": 1e3 * T, "T_N_ms": 1e3 * TN, "T/T_N": T / TN, "F/F_N": F / max(FN, 1.0),
                 "solved": ok, "solved_N": okn, "passes_max": st.passes, "passes_max_N": stn.passes,
                 "level_passes_per_signal": [v / Y.shape[0] for v in st.level_passes[:len(rc)]]}
+        if screened_exact:
+            # the same screening on the exact dictionary alone (the paper's GAP Safe FISTA curve)
+            TS, sts, oks = timed(d_exact, Y, lam, tol, algo=algo, rule=rule)
+            line.update({"T_S_ms": 1e3 * TS, "T_S/T_N": TS / TN, "solved_S": oks})
         print(json.dumps(line), flush=True)
 
+    fams = set(args.grid_families.split(","))
+
+    if "faust" in fams:
+        # the source-localisation stand-in: four sparse-factor levels, or only the finest one
+        wf = S.meg_faust(n_signals=50)
+        Yf = torch.tensor(wf.Y, dtype=torch.float32, device=dev)
+        dfx = pkg.Dictionary.dense(wf.A, dtype="f32").prepare()
+        lmf = dfx.lambda_max(Yf)
+        for name, levels in (("meg-faust4", wf.levels), ("meg-faust1", wf.levels[-1:])):
+            df = pkg.Dictionary.dense(wf.A, dtype="f32")
+            for facs in levels:
+                df.add_faust_level(facs)
+            df.prepare()
+            rcf = df.info()["rc"]
+            for tol in (1e-3, 1e-6):
+                point(name, df, dfx, rcf, Yf, lmf, 0.1, tol, screened_exact=True)
+            for ratio in (0.03, 0.3):
+                point(name, df, dfx, rcf, Yf, lmf, ratio, 1e-6, screened_exact=True)
+            df.close()
+        dfx.close()
+    if "gaussian" not in fams and "kron" not in fams:
+        return 0
+    if "gaussian" not in fams:
+        return _grid_kron(point, pkg, S, dev, ratios_grid)
     # Gaussian dictionary with the precision ladder
     w = S.paper_dense(n_signals=25)
     Y = torch.tensor(w.Y, dtype=torch.float32, device=dev)
@@ -461,7 +493,14 @@ def run_grid(args):
     point("gaussian+fp8/bf16", d, d_exact, rc, Y, lmax, 0.1, 1e-6, rule=1)
     d.close()
     d_exact.close()
-    # structured dictionaries: three error profiles
+    if "kron" in fams:
+        return _grid_kron(point, pkg, S, dev, ratios_grid)
+    return 0
+
+
+def _grid_kron(point, pkg, S, dev, ratios_grid):
+    """Grid points of the structured dictionaries: three error profiles of the Kronecker terms."""
+    import torch
     for decay in (0.3, 0.5, 0.7):
         wk = S.paper_kron(decay, n_signals=25)
         Yk = torch.tensor(wk.Y, dtype=torch.float32, device=dev)

@@ -55,7 +55,8 @@ typedef enum {
     LASSO_LEVEL_BF16 = 2,         /* BF16 copy of A (round to nearest even)                    */
     LASSO_LEVEL_FP8 = 3,          /* E4M3 copy with per-atom scale s_j = max_i |a_ij| / 448     */
     LASSO_LEVEL_KRON = 4,         /* Kronecker truncation to the first `param` terms            */
-    LASSO_LEVEL_F32 = 5           /* FP32 copy of an FP64 dictionary                            */
+    LASSO_LEVEL_F32 = 5,          /* FP32 copy of an FP64 dictionary                            */
+    LASSO_LEVEL_FAUST = 6         /* product of sparse factors (lasso_dict_add_level_faust)     */
 } lasso_level_kind;
 
 typedef struct lasso_dict lasso_dict;
@@ -80,6 +81,25 @@ int lasso_dict_create_kron(const float* B, const float* C, int R, int N1, int K1
  * computed exactly in FP64 against the exact atoms.  param: number of Kronecker terms for
  * LASSO_LEVEL_KRON, ignored otherwise.  Up to 7 approximate levels. */
 int lasso_dict_add_level(lasso_dict* dict, lasso_level_kind kind, int param);
+
+/* Append a product of sparse factors A~ = S_0 S_1 ... S_{J-1} as an approximate level (the
+ * FAuST dictionaries of Section VI, "multilayer sparse" approximations of A).  S_f has
+ * dims[f] rows and dims[f+1] columns, dims[0] = N and dims[J] = K; the product approximates the
+ * dictionary as stored (normalised atoms when the dictionary was created with normalize != 0),
+ * so a column scale belongs in the last factor.  All arrays are HOST memory, read once and
+ * copied:
+ *   indptr   concatenation over f of the dims[f] + 1 CSR row pointers of S_f (each factor's
+ *            own offsets, starting at 0 and non-decreasing);
+ *   indices  concatenation over f of the nnz_f = indptr_f[dims[f]] column indices of S_f,
+ *            strictly increasing within each row and in [0, dims[f+1]);
+ *   values   the matching FP32 values (finite).
+ * eps_j = ||a~_j - a_j||_2 is computed from the explicit FP64 product; the FP32 sparse
+ * products of a solve add their rounding through kappa_j = ||(|S_0| ... |S_{J-1}|) e_j||_2.
+ * RC defaults to (sum_f nnz_f) / (N K).  1 <= J <= 16, every nnz_f < 2^31.  Returns
+ * LASSO_ERR_INVALID_ARG when a check fails (nothing is added), LASSO_ERR_NOMEM when the
+ * explicit products (2 x K x max(dims) doubles, during the call only) do not fit. */
+int lasso_dict_add_level_faust(lasso_dict* dict, int J, const int64_t* dims, const int64_t* indptr,
+                               const int32_t* indices, const float* values);
 
 /* Set the relative complexity RC of level `level` (eq:complexity_model_approx) used by the
  * speed criterion of Algorithm 2; by default RC is the level's bytes (dense) or FLOPs
@@ -121,7 +141,9 @@ typedef struct {
     int max_iter;            /* per-signal pass limit (default 20000)                           */
     int lambda_relative;     /* 1: lambdas are lambda / lambda_max of each signal (default 0)   */
     int final_fp64;          /* 1: append an FP64-accumulation rung on the exact data and keep
-                                FP64 iterates (tight tolerances; default 0)                     */
+                                FP64 iterates (tight tolerances; default 0).  The gaps certify
+                                the FP64 iterates: lasso_solve returns them as they are, the
+                                batch calls return their rounding to FP32                      */
     int certify_full;        /* 1: audit with an explicit full-dictionary pass at exit (default
                                 0): every atom recomputed with error-free products            */
     int passes_per_sync;     /* passes per captured CUDA graph replay (default 8)               */
@@ -145,8 +167,10 @@ typedef struct {
                                 FP32 level (FP32 iterates at their precision floor, e.g. on very
                                 coherent dictionaries) is stopped and solved again from scratch
                                 with FP64 iterates and an FP64-accumulation rung, as final_fp64
-                                does; its outputs replace the FP32 ones.  0: such a signal ends
-                                with LASSO_ERR_MAXITER.                                          */
+                                does; its outputs replace the FP32 ones.  That second solve keeps
+                                its extrapolated point (the certified one) FP32-representable, so
+                                the returned gap covers the returned FP32 x.  0: such a signal
+                                ends with LASSO_ERR_MAXITER.                                     */
     int autotune;            /* 1 (default): before the first FP32 batch of a size class (B rounded
                                 up to a power of two), time the correlation pass for atom chunks
                                 of 64 / 128 / 256 and 4 / 8 / 16 blocks per SM on a synthetic
@@ -166,9 +190,9 @@ typedef struct {
     double seconds;          /* wall time of the call                                           */
     int64_t launches;        /* kernels launched by the call (all kinds)                        */
     /* per kernel kind (0 residual, 1 correlation + update, 2 screening, 3 schedule,
-       4 Kronecker GEMMs, 5 tensor-core GEMMs): launches, device milliseconds (with
-       opts.profile) and algorithmic bytes (dictionary rows, signals and iterates read or
-       written by the definition of the step) */
+       4 structured products (Kronecker GEMMs, sparse factors), 5 tensor-core GEMMs):
+       launches, device milliseconds (with opts.profile) and algorithmic bytes (dictionary
+       rows, signals and iterates read or written by the definition of the step) */
     int64_t kernel_launches[6];
     double kernel_ms[6];
     double kernel_bytes[6];

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("lasso_dict_create_dense", C.c_int, [P, C.c_int, I64, I64, I64, C.c_int, C.c_int, C.c_int, C.POINTER(P)]),
     ("lasso_dict_create_kron", C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(P)]),
     ("lasso_dict_add_level", C.c_int, [P, C.c_int, C.c_int]),
+    ("lasso_dict_add_level_faust", C.c_int, [P, C.c_int, P, P, P, P]),
     ("lasso_dict_set_rc", C.c_int, [P, C.c_int, C.c_double]),
     ("lasso_dict_prepare", C.c_int, [P, C.c_double]),
     ("lasso_dict_info", C.c_int, [P, C.POINTER(LassoDictInfo)]),

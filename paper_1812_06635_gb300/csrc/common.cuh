@@ -24,12 +24,27 @@ enum LevelKind : int {
   LK_BF16 = 2,    // BF16 data, FP32 products, compensated accumulation
   LK_FP8 = 3,     // E4M3 data with per-atom FP32 scale, FP32 products
   LK_KRON = 4,    // sum of Kronecker products, FP32 small GEMMs
-  LK_F32D = 5     // FP32 data, FP64 accumulation (final FP64 rung of an FP32 dictionary)
+  LK_F32D = 5,    // FP32 data, FP64 accumulation (final FP64 rung of an FP32 dictionary)
+  LK_FAUST = 6    // product of sparse factors (CSR), FP32 sparse products
 };
 
-__host__ __device__ inline bool level_is_dense(int k) { return k != LK_KRON; }
+// Structured levels form their products over every atom in batched kernels (A~ z into AZ,
+// A~^T rho into Gfull); the correlation pass only reads them.
+__host__ __device__ inline bool level_structured(int k) { return k == LK_KRON || k == LK_FAUST; }
+__host__ __device__ inline bool level_is_dense(int k) { return !level_structured(k); }
 enum ResModel : int { RES_FOLD = 0, RES_CHAIN = 1, RES_DOT2 = 2 };
 __host__ __device__ inline bool level_fp64_arith(int k) { return k == LK_F64 || k == LK_F32D; }
+
+// One sparse factor S_f (rows x cols) of a product level, in CSR and as the CSR of S_f^T.
+struct FaustFactor {
+  int rows, cols;
+  const int32_t* rp;        // rows + 1 row pointers
+  const int32_t* ci;        // column indices, increasing within a row
+  const float* v;
+  const int32_t* rpT;       // S_f^T: cols + 1 row pointers
+  const int32_t* ciT;
+  const float* vT;
+};
 
 // One rung of the ladder, as the kernels see it.
 struct LevelDev {
@@ -69,6 +84,10 @@ struct LevelDev {
   const float* C;
   const float* dscale;      // d_j as FP32 (the FP64 value enters through kappa / eps)
   int R, N1, K1, N2, K2;
+  // Product of sparse factors (LK_FAUST): A~ = S_0 S_1 ... S_{J-1} (device array of J factors);
+  // fdim = the largest dimension of any factor (length of the scratch vectors)
+  const FaustFactor* fac;
+  int J, fdim;
 };
 
 struct DictDev {
@@ -99,8 +118,10 @@ struct SigState {
   // screening scalars of the pass: |s'|, |s'| ||rho||, test radius, |s~|, R~, 1 / lam
   double t_abs_sp, t_c_eps, t_Rs, t_abs_st, t_Rt, t_inv_lam;
   int act, scr, snap, refine;        // outcome of the pass, screen flag, snapshot, tighten request
-  int res_tight, c_res_tight;        // residual with error-free products (this pass / the snapshot)
-  int corr_tight, pad3;              // exact level: correlations with error-free products (sticky)
+  int res_tight, c_res_tight;        // residual with error-free products (next passes, sticky / the snapshot)
+  int corr_tight;                    // exact level: correlations with error-free products (sticky)
+  int res_used;                      // the products the current pass's residual was formed with
+                                     // (k_residual): the rounding model of its bound follows it
   double best_cert;                  // exact level: best certificate so far
   int stall, pad2;                   // exact level: passes without a 2 % improvement of it
   int c_nnz, pending, next_check, pad1;
@@ -122,6 +143,8 @@ struct SolveParams {
   int full_gap;             // 1: stop on the full-dictionary gap (checked explicitly)
   int stall_passes;         // exact FP32 level: passes without progress that mark a signal saturated (0: off)
   int corr_grid;            // blocks of the correlation pass (the per-pass chunk keeps it busy)
+  int z_f32;                // FP64 iterates whose point is returned in FP32: the extrapolated point z
+                            // (the certified and returned point) is kept FP32-representable
 };
 
 // Internal status of a signal whose FP32 iterates stopped improving on the exact level: the
@@ -234,7 +257,7 @@ __device__ __forceinline__ double residual_bound(const LevelDev& L, double sum_k
                                                  bool vt64, bool fast) {
   const double urho = vt64 ? U64 : U32;
   // fast: FP32 residual as plain FMA chains over the nonzeros (one chain per row), then y - acc
-  if (fast && !vt64 && L.kind != LK_KRON && !level_fp64_arith(L.kind))
+  if (fast && !vt64 && !level_structured(L.kind) && !level_fp64_arith(L.kind))
     return gamma_n((double)n_nz + 4.0, U32) * sum_kapz + 2.0 * urho * nrho;
   switch (L.res_model) {
     case RES_CHAIN:

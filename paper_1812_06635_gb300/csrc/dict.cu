@@ -418,6 +418,84 @@ __global__ void k_pi_kron_m2(LevelDev L, const double* __restrict__ U, double* _
   }
 }
 
+// Products of sparse factors (FP64).  out = S v, or S^T v through the stored CSR of S^T.
+__global__ void k_faust_mv64(FaustFactor F, int transpose, const double* __restrict__ in, double* __restrict__ out) {
+  const int rows = transpose ? F.cols : F.rows;
+  const int32_t* rp = transpose ? F.rpT : F.rp;
+  const int32_t* ci = transpose ? F.ciT : F.ci;
+  const float* v = transpose ? F.vT : F.v;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < rows; n += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = rp[n]; p < rp[n + 1]; ++p) s = fma((double)v[p], in[ci[p]], s);
+    out[n] = s;
+  }
+}
+
+// Explicit product, atom-major: T[j, n] = S_{J-1}[n, j] for the last factor (|S| when absval;
+// the caller zeroes T; each (n, j) occurs once in a canonical CSR) ...
+__global__ void k_faust_last64(FaustFactor F, int absval, int64_t ld, double* __restrict__ T) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < F.rows; n += (int64_t)gridDim.x * blockDim.x)
+    for (int p = F.rp[n]; p < F.rp[n + 1]; ++p) {
+      const double v = F.v[p];
+      T[(int64_t)F.ci[p] * ld + n] = absval ? fabs(v) : v;
+    }
+}
+
+// ... then Tout[j, n] = sum over row n of S_f of S_f[n, c] Tin[j, c] for f = J-2, ..., 0.
+__global__ void k_faust_stage64(FaustFactor F, int absval, int64_t K, int64_t ld, const double* __restrict__ Tin,
+                                double* __restrict__ Tout) {
+  const int64_t total = K * F.rows;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / F.rows;
+    const int n = (int)(t % F.rows);
+    const double* row = Tin + j * ld;
+    double s = 0.0;
+    for (int p = F.rp[n]; p < F.rp[n + 1]; ++p) {
+      const double v = F.v[p];
+      s = fma(absval ? fabs(v) : v, row[F.ci[p]], s);
+    }
+    Tout[j * ld + n] = s;
+  }
+}
+
+// kappa_j = ||(|S_0| ... |S_{J-1}|) e_j|| from the explicit absolute product (warp per atom).
+__global__ void k_faust_kappa(const double* __restrict__ P, int64_t ld, int64_t N, int64_t K, double* __restrict__ kappa) {
+  int lane = threadIdx.x & 31;
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = w; j < K; j += nw) {
+    double s = 0.0;
+    for (int64_t n = lane; n < N; n += 32) s = fma(P[j * ld + n], P[j * ld + n], s);
+    s = warp_sum(s);
+    if (lane == 0) kappa[j] = sqrt(s) * (1.0 + 1e-12);
+  }
+}
+
+// eps_j = ||a~_j - a_j|| from the explicit product, plus gam64 kappa_j for its own FP64
+// evaluation (|P^ - P| <= gamma |S_0| ... |S_{J-1}| entrywise); ||a~_j|| rounded up.
+__global__ void k_faust_eps(const double* __restrict__ P, int64_t ld, const void* __restrict__ ex, int ex_kind,
+                            int64_t ldN, int64_t N, int64_t K, double gam64, const double* __restrict__ kappa,
+                            double* __restrict__ eps, float* __restrict__ atn) {
+  int lane = threadIdx.x & 31;
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = w; j < K; j += nw) {
+    double se = 0.0, sa = 0.0;
+    for (int64_t n = lane; n < N; n += 32) {
+      const double a = P[j * ld + n];
+      const double e = a - load_exact(ex, ex_kind, j * ldN + n);
+      se = fma(e, e, se);
+      sa = fma(a, a, sa);
+    }
+    se = warp_sum(se);
+    sa = warp_sum(sa);
+    if (lane == 0) {
+      eps[j] = sqrt(se) * (1.0 + 1e-12) + gam64 * kappa[j];
+      atn[j] = __double2float_ru((sqrt(sa) + gam64 * kappa[j]) * (1.0 + 1e-12));
+    }
+  }
+}
+
 __global__ void k_norm_scale(double* __restrict__ v, int64_t n, double* __restrict__ out_norm) {
   __shared__ double sh[32];
   double s = 0.0;
@@ -524,6 +602,15 @@ static void level_rounding(const lasso_dict* d, const HostLevel& h, bool vt_doub
       L.res_model = RES_FOLD;
       L.gam_res = gamma_n((double)d->K1 + (double)h.param * d->K2 + 5.0, U32);
       break;
+    case LK_FAUST:
+      // FP32 FMA chains along the CSR rows, one factor after the other: the stages' relative
+      // errors compose to gamma of the summed longest rows, weighted entrywise by
+      // |S_0| ... |S_{J-1}|, whose column norms are kappa_j
+      L.gam_corr = gamma_n((double)h.n_adj + 3.0, U32) + stage;
+      L.gam_tight = L.gam_corr;
+      L.res_model = RES_FOLD;
+      L.gam_res = gamma_n((double)h.n_fwd + 5.0, U32);
+      break;
   }
 }
 
@@ -549,9 +636,13 @@ static void free_level(HostLevel& h) {
   cudaFree(h.kappa);
   cudaFree(h.atnorm);
   for (auto* e : h.epsr32) cudaFree(e);
-  if (h.owns_data || h.kind == LK_KRON) {
+  if (h.owns_data || h.kind == LK_KRON || h.kind == LK_FAUST) {
     cudaFree(h.kappa32);
     cudaFree(h.eps32);
+  }
+  if (h.kind == LK_FAUST) {
+    cudaFree(h.fbuf);
+    cudaFree(h.fac);
   }
   cudaFree(h.split1);
   cudaFree(h.split2);
@@ -642,6 +733,11 @@ LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double,
     L.N2 = d->N2;
     L.K2 = d->K2;
   }
+  if (h.kind == LK_FAUST) {
+    L.fac = h.fac;
+    L.J = h.J;
+    L.fdim = h.fdim;
+  }
   return L;
 }
 
@@ -723,6 +819,7 @@ static int level_sq_norm(lasso_dict* d, const HostLevel& h, int iters, double* o
   int64_t tsz = 16;
   if (h.kind == LK_KRON)
     tsz = std::max<int64_t>((int64_t)h.param * d->K1 * d->N2, (int64_t)h.param * d->N1 * d->K2);
+  if (h.kind == LK_FAUST) tsz = 2 * (int64_t)h.fdim;
   if ((rc = alloc((void**)&tmp, tsz * sizeof(double)))) return rc;
   if ((rc = alloc((void**)&nrm, sizeof(double)))) return rc;
   k_fill<<<grid_for(K), 256>>>(v, K, 1.0 / std::sqrt((double)K));
@@ -730,7 +827,14 @@ static int level_sq_norm(lasso_dict* d, const HostLevel& h, int iters, double* o
   const int64_t kslice = 512;
   for (int it = 0; it < iters; ++it) {
     // w = A~ v
-    if (h.kind == LK_KRON) {
+    if (h.kind == LK_FAUST) {
+      const double* src = v;
+      for (int f = h.J - 1; f >= 0; --f) {
+        double* dst = f == 0 ? w : tmp + ((h.J - 1 - f) & 1) * (int64_t)h.fdim;
+        k_faust_mv64<<<grid_for(h.fac_h[f].rows), 256>>>(h.fac_h[f], 0, src, dst);
+        src = dst;
+      }
+    } else if (h.kind == LK_KRON) {
       k_pi_kron_m1<<<grid_for(tsz), 256>>>(L, v, d->d, tmp);
       k_pi_kron_m2<<<grid_for(N), 256>>>(L, tmp, w);
     } else {
@@ -739,7 +843,14 @@ static int level_sq_norm(lasso_dict* d, const HostLevel& h, int iters, double* o
       k_pi_matvec_dense<<<g, 128>>>(L, N, K, kslice, v, w);
     }
     // v = A~^T w
-    if (h.kind == LK_KRON) {
+    if (h.kind == LK_FAUST) {
+      const double* src = w;
+      for (int f = 0; f < h.J; ++f) {
+        double* dst = f == h.J - 1 ? v : tmp + (f & 1) * (int64_t)h.fdim;
+        k_faust_mv64<<<grid_for(h.fac_h[f].cols), 256>>>(h.fac_h[f], 1, src, dst);
+        src = dst;
+      }
+    } else if (h.kind == LK_KRON) {
       k_pi_kron_t1<<<grid_for(tsz), 256>>>(L, w, tmp);
       k_pi_kron_t2<<<grid_for(K), 256>>>(L, tmp, d->d, v);
     } else {
@@ -975,6 +1086,171 @@ extern "C" int lasso_dict_add_level(lasso_dict* d, lasso_level_kind kind, int pa
   return LASSO_OK;
 }
 
+void lasso_workspace_free(lasso::Workspace* ws);
+
+namespace {
+
+// Explicit FP64 product of the factors (|S_f| when absval), atom-major K x ld, into `out`
+// (`tmp` is the other buffer of the ping-pong).  Returns the buffer holding the result.
+double* faust_explicit(const HostLevel& h, int64_t K, int64_t ld, int absval, double* out, double* tmp) {
+  double* bufs[2] = {out, tmp};
+  // the last factor lands in the buffer that, after J - 1 stages, is `out`
+  int cur = (h.J - 1) & 1;
+  cudaMemsetAsync(bufs[cur], 0, (size_t)K * ld * sizeof(double));
+  k_faust_last64<<<grid_for(h.fac_h[h.J - 1].rows), 256>>>(h.fac_h[h.J - 1], absval, ld, bufs[cur]);
+  for (int f = h.J - 2; f >= 0; --f) {
+    k_faust_stage64<<<grid_for(K * h.fac_h[f].rows), 256>>>(h.fac_h[f], absval, K, ld, bufs[cur], bufs[cur ^ 1]);
+    cur ^= 1;
+  }
+  return bufs[cur];
+}
+
+}  // namespace
+
+extern "C" int lasso_dict_add_level_faust(lasso_dict* d, int J, const int64_t* dims, const int64_t* indptr,
+                                          const int32_t* indices, const float* values) {
+  if (!d || (int)d->approx.size() + 1 >= MAX_LEVELS - 1) return LASSO_ERR_INVALID_ARG;
+  if (J < 1 || J > 16 || !dims || !indptr || !indices || !values) return LASSO_ERR_INVALID_ARG;
+  for (int f = 0; f <= J; ++f)
+    if (dims[f] < 1 || dims[f] > (1 << 30)) return LASSO_ERR_INVALID_ARG;
+  if (dims[0] != d->N || dims[J] != d->K) return LASSO_ERR_INVALID_ARG;
+  // validate every factor on the host (so that every device index stays in range) and lay the
+  // CSR arrays of S_f and S_f^T out in one buffer, each array 16-byte aligned
+  struct Lay { int64_t rows, cols, nnz, rp, ci, v, rpT, ciT, vT; };
+  std::vector<Lay> lay(J);
+  int64_t po = 0, no = 0, bytes = 0, nnz_total = 0;
+  int n_fwd = 0, n_adj = 0, fdim = 0;
+  auto take = [&](int64_t b) { const int64_t at = bytes; bytes += round_up(std::max<int64_t>(b, 16), 16); return at; };
+  for (int f = 0; f < J; ++f) {
+    Lay& l = lay[f];
+    l.rows = dims[f];
+    l.cols = dims[f + 1];
+    const int64_t* rp = indptr + po;
+    if (rp[0] != 0) return LASSO_ERR_INVALID_ARG;
+    int64_t longest = 0;
+    for (int64_t n = 0; n < l.rows; ++n) {
+      if (rp[n + 1] < rp[n]) return LASSO_ERR_INVALID_ARG;
+      longest = std::max(longest, rp[n + 1] - rp[n]);
+    }
+    l.nnz = rp[l.rows];
+    if (l.nnz >= ((int64_t)1 << 31)) return LASSO_ERR_INVALID_ARG;
+    std::vector<int64_t> colcount(l.cols, 0);
+    for (int64_t n = 0; n < l.rows; ++n)
+      for (int64_t p = rp[n]; p < rp[n + 1]; ++p) {
+        const int32_t c = indices[no + p];
+        if (c < 0 || c >= l.cols) return LASSO_ERR_INVALID_ARG;
+        if (p > rp[n] && c <= indices[no + p - 1]) return LASSO_ERR_INVALID_ARG;
+        if (!std::isfinite(values[no + p])) return LASSO_ERR_INVALID_ARG;
+        ++colcount[c];
+      }
+    int64_t longest_t = 0;
+    for (int64_t c : colcount) longest_t = std::max(longest_t, c);
+    n_fwd += (int)longest;
+    n_adj += (int)longest_t;
+    fdim = std::max<int>(fdim, (int)std::max(l.rows, l.cols));
+    l.rp = take((l.rows + 1) * 4);
+    l.ci = take(l.nnz * 4);
+    l.v = take(l.nnz * 4);
+    l.rpT = take((l.cols + 1) * 4);
+    l.ciT = take(l.nnz * 4);
+    l.vT = take(l.nnz * 4);
+    nnz_total += l.nnz;
+    po += l.rows + 1;
+    no += l.nnz;
+  }
+  // host staging: CSR of S_f as given, CSR of S_f^T by a counting sort over the columns (rows of
+  // S_f^T keep the increasing order of the original rows)
+  std::vector<unsigned char> stage((size_t)bytes, 0);
+  po = 0;
+  no = 0;
+  for (int f = 0; f < J; ++f) {
+    const Lay& l = lay[f];
+    const int64_t* rp = indptr + po;
+    int32_t* rp32 = reinterpret_cast<int32_t*>(&stage[l.rp]);
+    int32_t* ci32 = reinterpret_cast<int32_t*>(&stage[l.ci]);
+    float* v32 = reinterpret_cast<float*>(&stage[l.v]);
+    int32_t* rpT = reinterpret_cast<int32_t*>(&stage[l.rpT]);
+    int32_t* ciT = reinterpret_cast<int32_t*>(&stage[l.ciT]);
+    float* vT = reinterpret_cast<float*>(&stage[l.vT]);
+    for (int64_t n = 0; n <= l.rows; ++n) rp32[n] = (int32_t)rp[n];
+    memcpy(ci32, indices + no, l.nnz * 4);
+    memcpy(v32, values + no, l.nnz * 4);
+    for (int64_t c = 0; c <= l.cols; ++c) rpT[c] = 0;
+    for (int64_t p = 0; p < l.nnz; ++p) ++rpT[ci32[p] + 1];
+    for (int64_t c = 0; c < l.cols; ++c) rpT[c + 1] += rpT[c];
+    std::vector<int32_t> next(rpT, rpT + l.cols);
+    for (int64_t n = 0; n < l.rows; ++n)
+      for (int64_t p = rp[n]; p < rp[n + 1]; ++p) {
+        const int32_t q = next[ci32[p]]++;
+        ciT[q] = (int32_t)n;
+        vT[q] = v32[p];
+      }
+    po += l.rows + 1;
+    no += l.nnz;
+  }
+  HostLevel h;
+  h.kind = LK_FAUST;
+  h.api_kind = LASSO_LEVEL_FAUST;
+  h.param = J;
+  h.owns_data = false;
+  h.J = J;
+  h.fdim = fdim;
+  h.n_fwd = n_fwd;
+  h.n_adj = n_adj;
+  const int64_t K = d->K, N = d->N, ldN = d->ldN;
+  const int64_t ld = std::max<int64_t>(fdim, ldN);
+  double *P = nullptr, *Q = nullptr;
+  int rc = LASSO_OK;
+  auto fail = [&](int code) {
+    cudaFree(P);
+    cudaFree(Q);
+    free_level(h);
+    return code;
+  };
+  if ((rc = alloc(&h.fbuf, (size_t)bytes))) return fail(rc);
+  if (cudaMemcpy(h.fbuf, stage.data(), (size_t)bytes, cudaMemcpyHostToDevice) != cudaSuccess) return fail(LASSO_ERR_CUDA);
+  unsigned char* base = static_cast<unsigned char*>(h.fbuf);
+  for (int f = 0; f < J; ++f) {
+    const Lay& l = lay[f];
+    FaustFactor F;
+    F.rows = (int)l.rows;
+    F.cols = (int)l.cols;
+    F.rp = reinterpret_cast<const int32_t*>(base + l.rp);
+    F.ci = reinterpret_cast<const int32_t*>(base + l.ci);
+    F.v = reinterpret_cast<const float*>(base + l.v);
+    F.rpT = reinterpret_cast<const int32_t*>(base + l.rpT);
+    F.ciT = reinterpret_cast<const int32_t*>(base + l.ciT);
+    F.vT = reinterpret_cast<const float*>(base + l.vT);
+    h.fac_h.push_back(F);
+  }
+  if ((rc = alloc((void**)&h.fac, J * sizeof(FaustFactor)))) return fail(rc);
+  if (cudaMemcpy(h.fac, h.fac_h.data(), J * sizeof(FaustFactor), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(LASSO_ERR_CUDA);
+  if ((rc = alloc_level_vectors(d, h))) return fail(rc);
+  if ((rc = alloc((void**)&P, (size_t)K * ld * sizeof(double)))) return fail(rc);
+  if ((rc = alloc((void**)&Q, (size_t)K * ld * sizeof(double)))) return fail(rc);
+  // kappa_j from |S_0| ... |S_{J-1}|, then eps_j and ||a~_j|| from the signed product
+  const double* Pa = faust_explicit(h, K, ld, 1, P, Q);
+  k_faust_kappa<<<grid_for(K * 32), 256>>>(Pa, ld, N, K, h.kappa);
+  const double* Pv = faust_explicit(h, K, ld, 0, P, Q);
+  k_faust_eps<<<grid_for(K * 32), 256>>>(Pv, ld, d->exact.data, d->exact.kind, ldN, N, K,
+                                         gamma_n((double)n_fwd + 2.0, U64), h.kappa, h.eps, h.atnorm);
+  if (cudaGetLastError() != cudaSuccess) return fail(LASSO_ERR_CUDA);
+  if ((rc = finish_level(d, h))) return fail(rc);
+  cudaFree(P);
+  cudaFree(Q);
+  P = Q = nullptr;
+  h.rc = (double)nnz_total / ((double)N * (double)K);
+  d->approx.push_back(h);
+  d->faust_dim = std::max(d->faust_dim, fdim);
+  d->prepared = false;
+  // the solve workspaces are sized for the levels they saw: rebuild them with this level's scratch
+  if (d->ws) lasso_workspace_free(d->ws);
+  if (d->ws64) lasso_workspace_free(d->ws64);
+  d->ws = d->ws64 = nullptr;
+  return LASSO_OK;
+}
+
 extern "C" int lasso_dict_set_rc(lasso_dict* d, int level, double rc) {
   if (!d || level < 0 || level > (int)d->approx.size() || !(rc > 0.0)) return LASSO_ERR_INVALID_ARG;
   HostLevel& h = level == (int)d->approx.size() ? d->exact : d->approx[level];
@@ -1018,7 +1294,7 @@ extern "C" int lasso_dict_level_host(const lasso_dict* d, int level, double* eps
   const HostLevel& h = level == (int)d->approx.size() ? d->exact : d->approx[level];
   if (eps_host) LASSO_CUDA_TRY(cudaMemcpy(eps_host, h.eps, d->K * 8, cudaMemcpyDeviceToHost));
   if (atoms_host) {
-    if (h.kind == LK_KRON) return LASSO_ERR_UNSUPPORTED;
+    if (level_structured(h.kind)) return LASSO_ERR_UNSUPPORTED;
     double* tmp = nullptr;
     int rc = alloc((void**)&tmp, (size_t)d->K * d->N * 8);
     if (rc) return rc;
@@ -1029,8 +1305,6 @@ extern "C" int lasso_dict_level_host(const lasso_dict* d, int level, double* eps
   }
   return LASSO_OK;
 }
-
-void lasso_workspace_free(lasso::Workspace* ws);
 
 extern "C" void lasso_dict_destroy(lasso_dict* d) {
   if (!d) return;

@@ -30,6 +30,12 @@ struct HostLevel {
   float* epsr32_split = nullptr;
   double c2 = 0.0;             // max_j ||a2_j|| / kappa_j (rounded up)
   float* dscale = nullptr;     // Kronecker d_j as FP32
+  // product of sparse factors: every CSR array in one allocation, the J descriptors on the device
+  void* fbuf = nullptr;
+  FaustFactor* fac = nullptr;
+  int J = 0, fdim = 0;
+  int n_fwd = 0, n_adj = 0;    // sum over factors of the longest row of S_f / of S_f^T
+  std::vector<FaustFactor> fac_h;   // host copy of the descriptors (device pointers)
   double u = U32, gam_corr = 0.0, gam_res = 0.0, rc = 1.0;
   bool rc_set = false;
   double eps_mean = 0.0, eps_max = 0.0;
@@ -52,6 +58,7 @@ struct lasso_dict {
   double* anorm = nullptr;             // K, exact atom norms (rounded up)
   float* anorm32 = nullptr;            // the same rounded up to FP32
   double anorm_max = 0.0;              // max_j ||a_j||
+  int faust_dim = 0;                   // largest factor dimension over the sparse-factor levels
   std::vector<lasso::HostLevel> approx;
   lasso::HostLevel exact;
   lasso::HostLevel rung64;             // FP64-accumulation rung on FP32 exact data (lazy)

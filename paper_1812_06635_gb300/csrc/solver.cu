@@ -56,6 +56,8 @@ struct Workspace {
   float* AZ = nullptr;               // B x ldN
   float* Xd = nullptr;               // B x K
   float* Tk = nullptr;               // B x R x max(K1 N2, N1 K2)
+  float* Fs = nullptr;               // sparse-factor levels: B x 2 x fdim scratch vectors
+  int64_t fs_ld = 0;                 // floats of scratch per signal
   void* rq[MAX_LEVELS] = {nullptr};  // tensor-core levels: quantised residuals (B slots x ldN)
   void* rq2[MAX_LEVELS] = {nullptr}; // split exact level: second BF16 part of the residuals
   float* rsig[MAX_LEVELS] = {nullptr};
@@ -71,7 +73,8 @@ void free_ws(Workspace* w) {
   if (!w) return;
   void* ptrs[] = {w->Yw, w->Rho, w->X, w->Z, w->G, w->Xout, w->nz_val, w->nz_idx, w->kept, w->c0ub,
                   w->mask, w->cand_idx, w->cand_val, w->offsets2, w->part_full,
-                  w->part_res, w->part_corr, w->offsets, w->counters, w->alg_bytes, w->st, w->Gfull, w->AZ, w->Xd, w->Tk};
+                  w->part_res, w->part_corr, w->offsets, w->counters, w->alg_bytes, w->st, w->Gfull, w->AZ, w->Xd, w->Tk,
+                  w->Fs};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < MAX_LEVELS; ++l) {
     cudaFree(w->rq[l]);
@@ -150,6 +153,12 @@ static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
     rc |= ws_alloc((void**)&w->Xd, BK * 4);
     rc |= ws_alloc((void**)&w->Tk, tk * 4);
   }
+  if (d->faust_dim > 0) {
+    w->fs_ld = 2 * (int64_t)d->faust_dim;
+    if (!w->Gfull) rc |= ws_alloc((void**)&w->Gfull, BK * 4);
+    if (!w->AZ) rc |= ws_alloc((void**)&w->AZ, BN * 4);
+    rc |= ws_alloc((void**)&w->Fs, (size_t)B * w->fs_ld * 4);
+  }
   rc |= ws_alloc((void**)&w->tc_err, 16);
   if (cudaHostAlloc((void**)&w->h_counters, 64, cudaHostAllocDefault) != cudaSuccess) rc |= 1;
   if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) rc |= 1;
@@ -192,6 +201,8 @@ struct PassArgs {
   float* AZ;
   float* Xd;
   float* Tk;
+  float* Fs;
+  int64_t fs_ld;
   int32_t* tc_slot;
   int32_t* tc_list;
   int64_t K, ldN;
@@ -242,6 +253,8 @@ static void fill_pass_args(PassArgs<VT>& pa, Workspace* w, const lasso_dict* d) 
   pa.AZ = w->AZ;
   pa.Xd = w->Xd;
   pa.Tk = w->Tk;
+  pa.Fs = w->Fs;
+  pa.fs_ld = w->fs_ld;
   pa.tc_slot = w->tc_slot;
   pa.tc_list = w->tc_list;
   pa.K = d->K;
@@ -446,7 +459,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
     const bool active = r0 < N;
     if (fp64a) {
       double out[4] = {0.0, 0.0, 0.0, 0.0};
-      if (L.kind == LK_KRON) {
+      if (level_structured(L.kind)) {
         if (active) {
           const float* az = a.AZ + (int64_t)b * a.ldN;
 #pragma unroll
@@ -496,7 +509,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
     DF acc[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v].init();
-    if (L.kind == LK_KRON) {
+    if (level_structured(L.kind)) {
       if (active) {
         const float* az = a.AZ + (int64_t)b * a.ldN;
 #pragma unroll
@@ -606,10 +619,11 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
     }
     sp->rr = rr;
     sp->yr = yr;
+    sp->res_used = tight ? 1 : 0;
     sp->nrho_ru = __double2float_ru(sqrt(rr));
     sp->thr_f = (float)(sp->lam * a.sp.inv_L);
     sp->beta_f = (float)sp->beta;
-    if (a.alg_bytes && L.kind != LK_KRON) {
+    if (a.alg_bytes && !level_structured(L.kind)) {
       // nonzero atoms of z (rows of A~), their values and indices, y read and rho written
       const double vs = (double)sizeof(VT);
       atomicAdd(&a.alg_bytes[0], (double)nnz * ((double)N * level_elem_bytes(L.kind) + 4.0 + vs) + 2.0 * N * vs);
@@ -675,7 +689,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
     double m1 = 0.0, m2 = 0.0;
     float m1f = 0.f, m2f = 0.f;
     const bool pair = MODE == CORR_PASS && !L.tc && (L.kind == LK_F32 || L.kind == LK_BF16 || L.kind == LK_FP8);
-    const bool from_full = L.kind == LK_KRON || (MODE == CORR_PASS && L.tc);
+    const bool from_full = level_structured(L.kind) || (MODE == CORR_PASS && L.tc);
     const float dq_f = from_full && L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
     constexpr int NW = CORR_THREADS / 32;
     for (int base = p0 + wid; base < p1; base += (pair ? 2 : 1) * NW) {
@@ -745,7 +759,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
             const double xn = v > thr ? v - thr : (v < -thr ? v + thr : 0.0);
             const double zn = a.sp.algo == LASSO_FISTA ? xn + s.beta * (xn - xj) : xn;
             X[j] = (VT)xn;
-            Z[j] = (VT)zn;
+            Z[j] = a.sp.z_f32 ? (VT)(float)zn : (VT)zn;
             G[pos] = (VT)g;
           }
         }
@@ -771,7 +785,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_corr(PassArgs<VT> a) {
       double* pc = a.part_corr + ((int64_t)b * a.nch + chunk) * 2;
       pc[0] = t1;
       pc[1] = t2;
-      if (MODE == CORR_PASS && a.alg_bytes && L.kind != LK_KRON && !L.tc) {
+      if (MODE == CORR_PASS && a.alg_bytes && !level_structured(L.kind) && !L.tc) {
         // preserved atoms of the chunk (rows of A~, index, x and z read and written, g written),
         // plus rho once per signal
         const double vs = (double)sizeof(VT);
@@ -824,7 +838,7 @@ __global__ void __launch_bounds__(CORR_THREADS, 4) k_corr_pass(PassArgs<VT> a) {
     const int p0 = chunk * CH, p1 = min(s.n_kept, p0 + CH);
     const VT* rho = a.Rho + (int64_t)b * a.ldN;
     const float nrho_f = s.nrho_ru, thr_f = s.thr_f, beta_f = s.beta_f;
-    const bool from_full = L.kind == LK_KRON || L.tc;
+    const bool from_full = level_structured(L.kind) || L.tc;
     const bool tight = !from_full && L.kind == LK_F32 && s.corr_tight;
     const float dq_f = L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
     const float gt_f = tight ? __double2float_ru(L.gam_tight) : 0.f;
@@ -1006,7 +1020,7 @@ __device__ PassScalars pass_scalars(const SigState& s, const LevelDev& L, double
   PassScalars o;
   const double lam = s.lam;
   const double nrho = sqrt(rr);
-  const double e_r = residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8, !s.res_tight);
+  const double e_r = residual_bound(L, s.sum_kapz, s.n_nz, nrho, sizeof(VT) == 8, !s.res_used);
   const double e = s.sum_epsz + e_r;
   double sp_ = 0.0, st_ = 0.0;
   if (rr > 0.0) {
@@ -1077,7 +1091,7 @@ __device__ void pass_decide(SigState& s, const PassArgs<VT>& a, double m1_bulk, 
     s.c_nnz = s.n_nz;
     s.c_m1 = m1_used;
     s.c_nrho_ru = __double2float_ru(nrho);
-    s.c_res_tight = s.res_tight;
+    s.c_res_tight = s.res_used;
   }
   // Dynamic Safe radius ||theta' - y/lam|| (Table I)
   const double sp_ = s.sp;
@@ -1973,6 +1987,72 @@ __global__ void k_kron_scatter(PassArgs<VT> a) {
   }
 }
 
+// ------------------------------------------------------------------ products of sparse factors
+
+// A~ z for signals on a sparse-factor level: one block per signal, factor after factor
+// (S_{J-1} first) over the signal's two scratch vectors, each output entry an FP32 FMA chain
+// along one CSR row.  z enters as a dense vector (scatter of its nonzero list); the last stage
+// writes A~ z into AZ (zero padding up to ldN), which the residual kernel reads.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_faust_fwd(PassArgs<VT> a) {
+  const int b = blockIdx.x;
+  const SigState& s = a.st[b];
+  if (s.done) return;
+  const LevelDev& L = a.dd.lv[s.level];
+  if (L.kind != LK_FAUST) return;
+  float* u = a.Fs + (int64_t)b * a.fs_ld;
+  float* w = u + a.fs_ld / 2;
+  for (int64_t j = threadIdx.x; j < a.K; j += blockDim.x) u[j] = 0.f;
+  __syncthreads();
+  for (int q = threadIdx.x; q < s.n_nz; q += blockDim.x)
+    u[a.nz_idx[(int64_t)b * a.K + q]] = (float)a.nz_val[(int64_t)b * a.K + q];
+  __syncthreads();
+  for (int f = L.J - 1; f >= 0; --f) {
+    const FaustFactor F = L.fac[f];
+    float* out = f == 0 ? a.AZ + (int64_t)b * a.ldN : w;
+    for (int n = threadIdx.x; n < F.rows; n += blockDim.x) {
+      float acc = 0.f;
+      for (int p = F.rp[n]; p < F.rp[n + 1]; ++p) acc = __fmaf_rn(F.v[p], u[F.ci[p]], acc);
+      out[n] = acc;
+    }
+    if (f == 0)
+      for (int64_t n = F.rows + threadIdx.x; n < a.ldN; n += blockDim.x) out[n] = 0.f;
+    __syncthreads();
+    float* t = u;
+    u = w;
+    w = t;
+  }
+}
+
+// A~^T rho for signals on a sparse-factor level: S_0^T first, through the stored CSR of each
+// S_f^T; the last stage writes every atom's correlation into Gfull.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_faust_adj(PassArgs<VT> a) {
+  const int b = blockIdx.x;
+  const SigState& s = a.st[b];
+  if (s.done) return;
+  const LevelDev& L = a.dd.lv[s.level];
+  if (L.kind != LK_FAUST) return;
+  float* u = a.Fs + (int64_t)b * a.fs_ld;
+  float* w = u + a.fs_ld / 2;
+  const VT* rho = a.Rho + (int64_t)b * a.ldN;
+  for (int n = threadIdx.x; n < a.dd.N; n += blockDim.x) u[n] = (float)rho[n];
+  __syncthreads();
+  for (int f = 0; f < L.J; ++f) {
+    const FaustFactor F = L.fac[f];
+    float* out = f == L.J - 1 ? a.Gfull + (int64_t)b * a.K : w;
+    for (int k = threadIdx.x; k < F.cols; k += blockDim.x) {
+      float acc = 0.f;
+      for (int p = F.rpT[k]; p < F.rpT[k + 1]; ++p) acc = __fmaf_rn(F.vT[p], u[F.ciT[p]], acc);
+      out[k] = acc;
+    }
+    __syncthreads();
+    float* t = u;
+    u = w;
+    w = t;
+  }
+}
+
 // ------------------------------------------------------------------ certificate and outputs
 
 // Full-dictionary certificate (a final pass over every atom with the most precise level):
@@ -2081,6 +2161,8 @@ struct SolveIO {
   int32_t* status = nullptr;
   int32_t* iters = nullptr;
   cudaStream_t stream = nullptr;
+  // the solve must certify the FP32 point it returns (second solve of saturated signals)
+  bool point_f32 = false;
 };
 
 // Events of one pass (profile mode): before residual stage, before correlation, before
@@ -2096,7 +2178,8 @@ struct TcJob {
 };
 
 template <typename VT>
-static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, int corr_grid, size_t corr_smem,
+static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, bool has_faust, int corr_grid,
+                        size_t corr_smem,
                         cudaEvent_t* ev, const std::vector<TcJob>& tc, int* tc_err, const TcJob* full_job) {
   const int B = pa.sp.B;
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
@@ -2117,6 +2200,7 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
     k_kron_gemm<VT, KS_U><<<dim3(tiles(K2), tiles(N1), B * Rmax), 256, 0, st>>>(pa);
     k_kron_gemm<VT, KS_Y><<<dim3(tiles(N2), tiles(N1), B), 256, 0, st>>>(pa);
   }
+  if (has_faust) k_faust_fwd<VT><<<B, 256, 0, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
   k_residual<VT><<<B, RES_THREADS, 0, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
@@ -2135,6 +2219,7 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
     k_kron_gemm<VT, KS_T><<<dim3(tiles(N2), tiles(K1), B * Rmax), 256, 0, st>>>(pa);
     k_kron_gemm<VT, KS_G><<<dim3(tiles(K2), tiles(K1), B), 256, 0, st>>>(pa);
   }
+  if (has_faust) k_faust_adj<VT><<<B, 256, 0, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[7], st, cudaEventRecordExternal);
   for (const TcJob& j : tc) {
     k_quant_rho<VT><<<B, 256, 0, st>>>(pa, j.lvl, j.fp8);
@@ -2169,8 +2254,8 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
 }
 
-static int pass_launches(bool has_kron, bool full_gap, int n_tc, bool tc_full) {
-  return (has_kron ? 12 : 7) + (full_gap ? (tc_full ? 5 : 3) : 0) + 2 * n_tc;
+static int pass_launches(bool has_kron, bool has_faust, bool full_gap, int n_tc, bool tc_full) {
+  return (has_kron ? 12 : 7) + (has_faust ? 2 : 0) + (full_gap ? (tc_full ? 5 : 3) : 0) + 2 * n_tc;
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -2302,10 +2387,11 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   if (!tc_jobs.empty() && !w->Gfull) {
     if (ws_alloc((void**)&w->Gfull, (size_t)w->B * d->K * 4)) return LASSO_ERR_NOMEM;
   }
-  bool has_kron = false;
+  bool has_kron = false, has_faust = false;
   int rmax = 0;
   for (int l = 0; l < pa.dd.n_levels; ++l) {
     has_kron |= pa.dd.lv[l].kind == LK_KRON;
+    has_faust |= pa.dd.lv[l].kind == LK_FAUST;
     if (pa.dd.lv[l].kind == LK_KRON) rmax = std::max(rmax, pa.dd.lv[l].R);
   }
   if (has_kron && B * rmax > 65535) return LASSO_ERR_UNSUPPORTED;
@@ -2321,6 +2407,8 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   pa.sp.B = (int)B;
   pa.sp.chunk = B >= 64 ? 4 * CORR_CHUNK : CORR_CHUNK;
   pa.sp.full_gap = o.full_gap ? 1 : 0;
+  // FP64 iterates that must certify the FP32 point they return keep that point FP32-representable
+  pa.sp.z_f32 = sizeof(VT) == 8 && io.point_f32 ? 1 : 0;
   // saturation of the FP32 iterates on the exact level: 200 passes without a 2 % better
   // certificate (a converging FISTA improves far faster), then the FP64 solve takes over
   pa.sp.stall_passes = sizeof(VT) == 4 && o.fp64_fallback && d->exact_kind == LK_F32 ? 200 : 0;
@@ -2390,7 +2478,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   }
   double kms[6] = {0, 0, 0, 0, 0, 0};
   for (int i = 0; i < k; ++i)
-    launch_pass<VT>(pa, st, has_kron, corr_grid, corr_smem, o.profile ? &evs[(size_t)i * PASS_EVENTS] : nullptr,
+    launch_pass<VT>(pa, st, has_kron, has_faust, corr_grid, corr_smem, o.profile ? &evs[(size_t)i * PASS_EVENTS] : nullptr,
                     tc_jobs, w->tc_err, full_job);
   cudaError_t ce = cudaStreamEndCapture(st, &graph);
   if (ce != cudaSuccess) {
@@ -2452,7 +2540,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   double hbytes[16] = {0};
   LASSO_CUDA_TRY(cudaMemcpyAsync(hbytes, w->alg_bytes, sizeof(hbytes), cudaMemcpyDeviceToHost, st));
   LASSO_CUDA_TRY(cudaStreamSynchronize(st));
-  int64_t launches = 6 + replays * (int64_t)k * pass_launches(has_kron, pa.sp.full_gap != 0, (int)tc_jobs.size(), full_job != nullptr);
+  int64_t launches = 6 + replays * (int64_t)k * pass_launches(has_kron, has_faust, pa.sp.full_gap != 0, (int)tc_jobs.size(), full_job != nullptr);
   {
     int herr = 0;
     LASSO_CUDA_TRY(cudaMemcpy(&herr, w->tc_err, 4, cudaMemcpyDeviceToHost));
@@ -2490,7 +2578,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     stats->launches = launches;
     stats->corr_chunk = pa.sp.chunk;
     stats->corr_blocks_per_sm = corr_bps;
-    const int per_pass[6] = {1, 1, pa.sp.full_gap ? 4 : 1, 1, has_kron ? 5 : 0, 2 * (int)tc_jobs.size()};
+    const int per_pass[6] = {1, 1, pa.sp.full_gap ? 4 : 1, 1, (has_kron ? 5 : 0) + (has_faust ? 2 : 0), 2 * (int)tc_jobs.size()};
     for (int q = 0; q < 6; ++q) {
       stats->kernel_launches[q] = replays * (int64_t)k * per_pass[q];
       stats->kernel_ms[q] = kms[q];
@@ -2617,6 +2705,7 @@ static int fp64_fallback(lasso_dict* d, Workspace* w, SolveIO& io, lasso_stats* 
   sub.opts.final_fp64 = 1;
   sub.opts.lambda_relative = 0;
   sub.opts.fp64_fallback = 0;
+  sub.point_f32 = true;
   sub.Xf = Xs;
   sub.gaps = gs;
   sub.status = ss;

@@ -11,7 +11,7 @@ import numpy as np
 
 from . import _native as nat
 
-LEVEL_BF16, LEVEL_FP8, LEVEL_KRON, LEVEL_F32 = 2, 3, 4, 5
+LEVEL_BF16, LEVEL_FP8, LEVEL_KRON, LEVEL_F32, LEVEL_FAUST = 2, 3, 4, 5, 6
 FISTA, ISTA = 0, 1
 RULE_GAP, RULE_DST, RULE_STATIC = 0, 1, 2
 STATUS = {0: "ok", -1: "invalid_arg", -2: "cuda", -3: "nonfinite", -4: "maxiter", -5: "timeout",
@@ -109,6 +109,22 @@ class Dictionary:
 
     def add_level(self, kind: int, param: int = 0) -> "Dictionary":
         nat.check(nat.load().lasso_dict_add_level(self._h, kind, param), "lasso_dict_add_level")
+        return self
+
+    def add_faust_level(self, factors) -> "Dictionary":
+        """Append A~ = S_0 S_1 ... S_{J-1} (sparse factors, coarsest levels first).  ``factors``:
+        CSR matrices (anything with ``shape``, ``indptr``, ``indices``, ``data``, e.g. scipy's),
+        column indices increasing within each row; values are stored as FP32."""
+        dims = [int(factors[0].shape[0])] + [int(f.shape[1]) for f in factors]
+        for f, (r, c) in zip(factors, zip(dims[:-1], dims[1:])):
+            if tuple(f.shape) != (r, c):
+                raise ValueError("inner dimensions of consecutive factors must agree")
+        d = np.asarray(dims, dtype=np.int64)
+        ip = np.ascontiguousarray(np.concatenate([np.asarray(f.indptr, np.int64) for f in factors]))
+        ix = np.ascontiguousarray(np.concatenate([np.asarray(f.indices, np.int32) for f in factors]))
+        vv = np.ascontiguousarray(np.concatenate([np.asarray(f.data, np.float32) for f in factors]))
+        nat.check(nat.load().lasso_dict_add_level_faust(self._h, len(factors), _ptr(d), _ptr(ip), _ptr(ix), _ptr(vv)),
+                  "lasso_dict_add_level_faust")
         return self
 
     def set_rc(self, level: int, rc: float) -> "Dictionary":

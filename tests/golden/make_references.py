@@ -1,10 +1,12 @@
 """Write the oracle reference solutions used by the GPU tests (calls only oracle/ and synthetic/).
 
-    python tests/golden/make_references.py
+    python tests/golden/make_references.py [c3|meg_faust]   (both when no name is given)
 
 c3_reference.npz: for a few signals of the c3 batch (2048 x 8192, seed 0) the Lasso minimiser at
 lambda = ratio * lambda_max, computed by the FP64 oracle (FISTA + GAP Safe, then the KKT-verified
 support system), stored sparsely (support, values), with lambda_max and lambda.
+meg_faust_reference.npz: the same for sampled signals of the source-localisation stand-in
+(204 x 8193 dense A, 50 signals, lambda = 0.1 lambda_max, seed 0).
 """
 import os
 import sys
@@ -19,6 +21,7 @@ from oracle import lasso as OL             # noqa: E402
 from oracle import solvers as OS           # noqa: E402
 
 C3_SIGNALS = (0, 1, 2, 4095)
+MEG_SIGNALS = (0, 23, 49)
 
 
 def minimiser(A, y, lam):
@@ -30,10 +33,9 @@ def minimiser(A, y, lam):
     raise RuntimeError("oracle did not identify the support")
 
 
-def c3_reference(path):
-    w = S.c3(n_signals=4096)
+def sampled_reference(path, w, signals):
     out = {}
-    for b in C3_SIGNALS:
+    for b in signals:
         y = w.Y[b]
         lm = OL.lambda_max(w.A.T @ y)
         lam = float(w.lam_ratio[b]) * lm
@@ -44,9 +46,13 @@ def c3_reference(path):
         out[f"s{b}_lmax"] = np.array(lm)
         out[f"s{b}_lam"] = np.array(lam)
         print(b, "support", S_.size, "lambda/lambda_max", w.lam_ratio[b])
-    out["signals"] = np.array(C3_SIGNALS)
+    out["signals"] = np.array(signals)
     np.savez_compressed(path, **out)
 
 
 if __name__ == "__main__":
-    c3_reference(os.path.join(HERE, "c3_reference.npz"))
+    which = sys.argv[1:] or ["c3", "meg_faust"]
+    if "c3" in which:
+        sampled_reference(os.path.join(HERE, "c3_reference.npz"), S.c3(n_signals=4096), C3_SIGNALS)
+    if "meg_faust" in which:
+        sampled_reference(os.path.join(HERE, "meg_faust_reference.npz"), S.meg_faust(n_signals=50), MEG_SIGNALS)

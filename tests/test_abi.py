@@ -45,6 +45,7 @@ def test_host_only_calls(lib):
     assert lib.lasso_dict_create_dense(None, 1, 10, 10, 10, 1, 0, 1, C.byref(h)) == -1
     assert lib.lasso_dict_create_kron(None, None, 1, 2, 2, 2, 2, 1, C.byref(h)) == -1
     assert lib.lasso_dict_add_level(None, 2, 0) == -1
+    assert lib.lasso_dict_add_level_faust(None, 1, None, None, None, None) == -1
     assert lib.lasso_solve(None, None, 1.0, 1e-6, None, None, None, None, None, None) == -1
 
 
