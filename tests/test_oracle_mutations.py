@@ -6,8 +6,12 @@ a missing clip) and runs a pin from ``test_oracle_problem``; the pin must raise.
 import numpy as np
 import pytest
 
+import test_oracle_dicts as TD
 import test_oracle_problem as P
+import test_oracle_regions as TR
+from oracle import dictionaries as D
 from oracle import lasso as L
+from oracle import regions as G
 
 
 def _wrong_threshold(v, u):
@@ -42,5 +46,71 @@ CASES = [
 @pytest.mark.parametrize("name,bad,pin", CASES, ids=[c[0] for c in CASES])
 def test_planted_mistake_is_caught(monkeypatch, name, bad, pin):
     monkeypatch.setattr(L, name, bad)
+    with pytest.raises((AssertionError, Exception)):
+        pin()
+
+
+# ----------------------------------------------------------------------------- zones, domes, factors
+
+def _C_pq_flipped(N, p, q):
+    inv_pstar = 1.0 - (0.0 if np.isinf(p) else 1.0 / p)
+    inv_q = 0.0 if np.isinf(q) else 1.0 / q
+    return float(N) ** max(inv_q - inv_pstar, 0.0)
+
+
+def _zone_test_without_eps_term(a_t, eps, c, R, p, q):
+    return abs(float(a_t @ c)) + R * float(G.lq_norm(a_t, G.conjugate(p))) + G.C_pq(a_t.size, p, q) * R * eps
+
+
+def _dome_max_wrong_offset_sign(a, c, R, n, psi):
+    an, nn = float(np.linalg.norm(a)), float(np.linalg.norm(n))
+    d = psi - float(n @ c)
+    if R * float(n @ a) / an <= d:
+        return float(a @ c) + R * an
+    nh = n / nn
+    alpha = float(a @ nh)
+    h = d / nn
+    return float(a @ c) - alpha * h + float(np.linalg.norm(a - alpha * nh)) * float(np.sqrt(max(R * R - h * h, 0.0)))
+
+
+def _scaling_q_with_l2_norm(Atz, eps, z, q):
+    m = float(np.max(np.abs(Atz) + eps * float(np.linalg.norm(z))))
+    return 1.0 / max(1.0, m)
+
+
+def _apply_t_through_rows(fac, v):
+    rows, cols, row_of, col, val = fac
+    out = np.zeros(cols)
+    np.add.at(out, np.minimum(row_of, cols - 1), val * v[np.minimum(col, rows - 1)])
+    return out
+
+
+def _matvec_wrong_order(self, x, idx=None):
+    v = np.zeros(self.K)
+    if idx is None:
+        v[:] = x
+    else:
+        v[idx] = x
+    for fac in self.f:                       # S_0 applied first instead of last
+        rows, cols, row_of, col, val = fac
+        v = np.bincount(row_of, weights=val * v[np.minimum(col, v.size - 1)], minlength=rows)
+    return v
+
+
+REGION_CASES = [
+    (G, "C_pq", _C_pq_flipped, lambda: TR.test_C_pq_against_extreme_points(3, 3.0)),
+    (G, "zone_sphere_test", _zone_test_without_eps_term,
+     lambda: TR.test_zone_sphere_test_bounds_sampled_pairs(2.0, np.inf)),
+    (G, "dome_max", _dome_max_wrong_offset_sign, lambda: TR.test_dome_max_matches_constrained_maximisation()),
+    (G, "stable_scaling_q", _scaling_q_with_l2_norm, lambda: TR.test_lemma2_with_lq_errors_gives_feasible_dual_points(np.inf)),
+    (D.FaustDict, "_apply_t", staticmethod(_apply_t_through_rows),
+     lambda: TD.test_faust_operator_against_explicit_product((6, 9, 13))),
+    (D.FaustDict, "matvec", _matvec_wrong_order, lambda: TD.test_faust_operator_against_explicit_product((6, 9, 13))),
+]
+
+
+@pytest.mark.parametrize("owner,name,bad,pin", REGION_CASES, ids=[c[1] for c in REGION_CASES])
+def test_planted_mistake_in_regions_and_factors_is_caught(monkeypatch, owner, name, bad, pin):
+    monkeypatch.setattr(owner, name, bad)
     with pytest.raises((AssertionError, Exception)):
         pin()

@@ -134,6 +134,26 @@ def test_lemma2_with_lq_errors_gives_feasible_dual_points(q):
         th = alpha * z
         assert np.max(np.abs(A.T @ th)) <= 1 + 1e-12
         assert np.max(np.abs(At.T @ th)) <= 1 + 1e-12
+    # adversarial errors that attain Hoelder's bound: a_j = a~_j + s_j eps_j u with u^T z = ||z||_{q*}
+    # and s_j the sign of a_j^T z, so |a_j^T z| = |a~_j^T z| + eps_j ||z||_{q*} and the scaled point
+    # touches the boundary of the feasible set (any smaller scaling denominator leaves it)
+    A = rng.standard_normal((N, K))
+    z = rng.standard_normal(N)
+    if np.isinf(q):
+        u = np.sign(z)
+    elif q == 1.0:
+        u = np.zeros(N)
+        k = int(np.argmax(np.abs(z)))
+        u[k] = np.sign(z[k])
+    else:
+        u = z / np.linalg.norm(z)
+    zq = float(u @ z)
+    s = np.sign(A.T @ z)
+    eps = 0.5 * np.abs(A.T @ z) / zq * rng.random(K)
+    At = A - (s * eps)[None, :] * u[:, None]
+    np.testing.assert_allclose(G.error_columns_lq(At, A, q), eps, rtol=1e-9)
+    th = G.stable_scaling_q(At.T @ z, eps, z, q) * z
+    assert np.max(np.abs(A.T @ th)) == pytest.approx(1.0, rel=1e-12)
 
 
 @pytest.mark.parametrize("q", QS)
