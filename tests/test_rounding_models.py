@@ -1,0 +1,90 @@
+"""The rounding models folded into the bounds, checked on CPU emulations of the arithmetic.
+
+The sparse-factor levels form A~^T rho and A~ z as FP32 FMA chains along CSR rows, one factor
+after another (the chains of the kernels that evaluate products of sparse factors).  Their
+bounds claim
+    |g^_j - a~_j^T rho| <= gamma_{n_adj + 3} kappa_j ||rho||,
+    ||AZ^ - A~ z||      <= gamma_{n_fwd + 5} sum_j kappa_j |z_j|,
+with kappa_j = ||(|S_0| ... |S_{J-1}|) e_j||, n_fwd / n_adj the summed longest rows of the S_f /
+of the S_f^T, gamma_n = n u / (1 - n u), u = 2^-24 (a reading of Section III-B: the paper
+treats products as exact).  Here each FMA is emulated as one rounding to FP32 of the exact
+product-sum (the product of two FP32 numbers is exact in FP64; the sum is then correctly
+rounded twice, FP64 then FP32, which can only exceed one FP32 rounding by a factor 1 + 2^-29)."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import dictionaries as D
+
+U = 2.0 ** -24
+
+
+def gamma(n):
+    return n * U / (1.0 - n * U)
+
+
+def _fma_chain_csr(indptr, indices, data, v):
+    """out_i = FMA chain over row i (in stored order), every step rounded to FP32."""
+    out = np.zeros(len(indptr) - 1, dtype=np.float32)
+    for i in range(len(indptr) - 1):
+        acc = np.float32(0.0)
+        for p in range(indptr[i], indptr[i + 1]):
+            acc = np.float32(float(acc) + float(np.float32(data[p])) * float(v[indices[p]]))
+        out[i] = acc
+    return out
+
+
+def _longest_row(M):
+    return int(np.max(np.diff(M.indptr))) if M.shape[0] else 0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_sparse_factor_chains_stay_within_their_bounds(seed):
+    w = S.faust_small(N=48, K=160, n_signals=4, seed=seed, levels=((2, 2), (4, 5), (6, 6)))
+    rng = np.random.default_rng(seed)
+    for facs in w.levels:
+        op = D.FaustDict(facs)
+        kappa = np.linalg.norm(op.abs_dense(), axis=0)
+        n_fwd = sum(_longest_row(F) for F in facs)
+        n_adj = sum(_longest_row(F.T.tocsr()) for F in facs)
+        # adjoint: FP32 rho, S_0^T first
+        rho = rng.standard_normal(op.N).astype(np.float32)
+        v = rho
+        for F in facs:
+            Ft = F.T.tocsr()
+            v = _fma_chain_csr(Ft.indptr, Ft.indices, Ft.data, v)
+        g_exact = op.rmatvec(rho.astype(np.float64))
+        err = np.abs(v.astype(np.float64) - g_exact)
+        bound = gamma(n_adj + 3) * kappa * float(np.linalg.norm(rho.astype(np.float64)))
+        assert np.all(err <= bound), float(np.max(err / bound))
+        # forward: FP32 z with a few nonzeros, S_{J-1} first
+        z = np.zeros(op.K, dtype=np.float32)
+        nz = rng.choice(op.K, 12, replace=False)
+        z[nz] = rng.standard_normal(12).astype(np.float32)
+        v = z
+        for F in reversed(facs):
+            v = _fma_chain_csr(F.indptr, F.indices, F.data, v)
+        az_exact = op.matvec(z.astype(np.float64))
+        err_f = float(np.linalg.norm(v.astype(np.float64) - az_exact))
+        assert err_f <= gamma(n_fwd + 5) * float(np.sum(kappa * np.abs(z.astype(np.float64))))
+
+
+def test_bound_is_not_vacuous():
+    """The observed chain errors are a visible fraction of the bound on adversarial data (all
+    positive entries, so nothing cancels), i.e. the model is not loose by orders of magnitude."""
+    w = S.faust_small(N=48, K=160, n_signals=1, seed=7, levels=((6, 6),))
+    facs = [F.copy() for F in w.levels[0]]
+    for F in facs:
+        F.data = np.abs(F.data).astype(np.float32).astype(np.float64)
+    op = D.FaustDict(facs)
+    kappa = np.linalg.norm(op.abs_dense(), axis=0)
+    n_adj = sum(_longest_row(F.T.tocsr()) for F in facs)
+    rho = (1.0 + np.random.default_rng(0).random(op.N)).astype(np.float32)
+    v = rho
+    for F in facs:
+        Ft = F.T.tocsr()
+        v = _fma_chain_csr(Ft.indptr, Ft.indices, Ft.data, v)
+    err = np.abs(v.astype(np.float64) - op.rmatvec(rho.astype(np.float64)))
+    bound = gamma(n_adj + 3) * kappa * float(np.linalg.norm(rho.astype(np.float64)))
+    assert np.all(err <= bound)
+    assert float(np.max(err / bound)) > 1e-3
