@@ -88,3 +88,101 @@ def test_bound_is_not_vacuous():
     bound = gamma(n_adj + 3) * kappa * float(np.linalg.norm(rho.astype(np.float64)))
     assert np.all(err <= bound)
     assert float(np.max(err / bound)) > 1e-3
+
+
+# ----------------------------------------------------------------------------- dense FP32 level
+
+def _fma32(acc, a, r):
+    return np.float32(float(acc) + float(a) * float(r))
+
+
+def _round_up16(n):
+    return (n + 15) // 16 * 16
+
+
+def _emulate_pair_fma_dot(a, r):
+    """The bulk correlation of an FP32 atom (the two-accumulator lane chains of the correlation
+    pass): lane l takes the float4 groups l, l + 64, ... into one accumulator and l + 32, l + 96, ...
+    into the other, the two are added, then a 5-level butterfly over the 32 lanes."""
+    nv = a.size // 4
+    lanes = np.zeros(32, dtype=np.float32)
+    for lane in range(32):
+        s0 = s1 = np.float32(0.0)
+        k = lane
+        while k + 32 < nv:
+            for e in range(4):
+                s0 = _fma32(s0, a[4 * k + e], r[4 * k + e])
+            for e in range(4):
+                s1 = _fma32(s1, a[4 * (k + 32) + e], r[4 * (k + 32) + e])
+            k += 64
+        if k < nv:
+            for e in range(4):
+                s0 = _fma32(s0, a[4 * k + e], r[4 * k + e])
+        lanes[lane] = np.float32(float(s0) + float(s1))
+    m = 16
+    while m:
+        lanes = np.array([np.float32(float(lanes[i]) + float(lanes[i ^ m])) for i in range(32)], dtype=np.float32)
+        m >>= 1
+    return float(lanes[0])
+
+
+def _two_sum(a, b):
+    s = np.float32(a + b)
+    bb = np.float32(s - a)
+    e = np.float32(np.float32(a - np.float32(s - bb)) + np.float32(b - bb))
+    return s, e
+
+
+def _emulate_dot2(a, r):
+    """Dot2 as the error-free correlation of the exact level: per lane a double-float (s, c) fed by
+    exact product splits p + q and TwoSum, a butterfly of merges, then s + c rounded to FP32."""
+    nv = a.size // 4
+    S_ = np.zeros(32, dtype=np.float32)
+    C_ = np.zeros(32, dtype=np.float32)
+    for lane in range(32):
+        s = c = np.float32(0.0)
+        for k in range(lane, nv, 32):
+            for e in range(4):
+                x, y = a[4 * k + e], r[4 * k + e]
+                p = np.float32(float(x) * float(y))
+                q = np.float32(float(x) * float(y) - float(p))      # exact
+                t, err = _two_sum(s, p)
+                s = t
+                c = np.float32(c + np.float32(err + q))
+        S_[lane], C_[lane] = s, c
+    m = 16
+    while m:
+        nS, nC = S_.copy(), C_.copy()
+        for i in range(32):
+            t, err = _two_sum(S_[i], S_[i ^ m])
+            nS[i] = t
+            nC[i] = np.float32(np.float32(C_[i] + C_[i ^ m]) + err)
+        S_, C_ = nS, nC
+        m >>= 1
+    return float(np.float32(S_[0] + C_[0]))
+
+
+@pytest.mark.parametrize("N", [100, 2048, 2500])
+def test_fp32_level_correlation_models(N):
+    """Bulk FMA chains stay within gamma_{nl + 2} sum |a_i rho_i| with nl = ld/32 + 8 (ld = N rounded
+    up to 16), and Dot2 within 2 gamma_{2 nl}^2 sum |a_i rho_i| plus the final rounding; random and
+    cancellation-free (all positive) data."""
+    import math
+    ld = _round_up16(N)
+    nl = math.ceil(ld / 32.0) + 8
+    rng = np.random.default_rng(N)
+    for trial in range(4):
+        a = np.zeros(ld, dtype=np.float32)
+        r = np.zeros(ld, dtype=np.float32)
+        if trial < 2:
+            a[:N] = rng.standard_normal(N).astype(np.float32)
+            r[:N] = rng.standard_normal(N).astype(np.float32)
+        else:
+            a[:N] = (1.0 + rng.random(N)).astype(np.float32)
+            r[:N] = (1.0 + rng.random(N)).astype(np.float32)
+        exact = math.fsum(float(x) * float(y) for x, y in zip(a, r))
+        mag = math.fsum(abs(float(x) * float(y)) for x, y in zip(a, r))
+        g_fast = _emulate_pair_fma_dot(a, r)
+        assert abs(g_fast - exact) <= gamma(nl + 2) * mag
+        g_tight = _emulate_dot2(a, r)
+        assert abs(g_tight - exact) <= 2.0 * gamma(2 * nl) ** 2 * mag + 3.0 * U * abs(g_tight)
