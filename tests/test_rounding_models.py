@@ -186,3 +186,49 @@ def test_fp32_level_correlation_models(N):
         assert abs(g_fast - exact) <= gamma(nl + 2) * mag
         g_tight = _emulate_dot2(a, r)
         assert abs(g_tight - exact) <= 2.0 * gamma(2 * nl) ** 2 * mag + 3.0 * U * abs(g_tight)
+
+
+# ----------------------------------------------------------------------------- residual
+
+def _emulate_residual_row(yv, w, a_col, d2):
+    """One row of the residual y - sum_q w_q a_{j_q}: an FMA chain over the nonzeros (d2 false) or
+    Dot2 into a double-float (s, c), then y - (s + c) through TwoSum(y, -s) and the small terms."""
+    s = c = np.float32(0.0)
+    for wq, aq in zip(w, a_col):
+        if d2:
+            p = np.float32(float(wq) * float(aq))
+            q = np.float32(float(wq) * float(aq) - float(p))
+            t, err = _two_sum(s, p)
+            s = t
+            c = np.float32(c + np.float32(err + q))
+        else:
+            s = _fma32(s, wq, aq)
+    t, e = _two_sum(np.float32(yv), np.float32(-s))
+    return float(np.float32(t + np.float32(e - c)))
+
+
+@pytest.mark.parametrize("nnz", [1, 7, 40])
+def test_fp32_residual_models(nnz):
+    """The residual bounds: FMA chains gamma_{nnz+4} sum_j kappa_j |z_j| + 2u ||rho^||, Dot2
+    3 gamma_{2 nnz + 2}^2 sum_j kappa_j |z_j| + 2u ||rho^|| (kappa_j = ||a_j||; FP32 iterates)."""
+    rng = np.random.default_rng(nnz)
+    N = 300
+    for trial in range(3):
+        A = rng.standard_normal((N, nnz)).astype(np.float32)
+        if trial == 2:
+            A = np.abs(A)
+        z = rng.standard_normal(nnz).astype(np.float32)
+        y = (A.astype(np.float64) @ z.astype(np.float64) + 0.3 * rng.standard_normal(N)).astype(np.float32)
+        exact = y.astype(np.float64) - A.astype(np.float64) @ z.astype(np.float64)
+        kap = np.linalg.norm(A.astype(np.float64), axis=0)
+        skz = float(np.sum(kap * np.abs(z.astype(np.float64))))
+        for d2 in (False, True):
+            rho = np.array([_emulate_residual_row(y[i], z, A[i], d2) for i in range(N)])
+            err = float(np.linalg.norm(rho - exact))
+            nr = float(np.linalg.norm(rho))
+            if d2:
+                g = gamma(2 * nnz + 2)
+                bound = 3.0 * g * g * skz + 2.0 * U * nr
+            else:
+                bound = gamma(nnz + 4) * skz + 2.0 * U * nr
+            assert err <= bound, (d2, err, bound)
