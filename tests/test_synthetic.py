@@ -74,3 +74,28 @@ def test_reproducible_and_prefix_shardable(first):
     # another seed changes everything
     c = S.c3(n_signals=4, first=first, N=64, K=128, seed=1)
     assert not np.array_equal(a.Y, c.Y) and not np.array_equal(a.A, c.A)
+
+
+def test_faust_recipe_factors_values_and_prefix():
+    """Sparse-factor stand-in: FP32 values everywhere, canonical CSR factors with the stated
+    entries per row (S_0, S_1) and per column (S_2), nested levels (each keeps a superset of the
+    previous level's entries), unit atoms, 8-sparse unit-norm signals, prefix-shardable."""
+    levels = ((3, 4), (4, 5))
+    w = S.meg_faust(n_signals=5, levels=levels)
+    assert _is_f32(w.A) and _is_f32(w.Y)
+    np.testing.assert_allclose(np.linalg.norm(w.A, axis=0), 1.0, atol=1e-6)
+    for (m0, m2), facs in zip(levels, w.levels):
+        S0, S1, S2 = facs
+        for F in facs:
+            assert F.has_canonical_format and _is_f32(F.data)
+            assert np.all(np.diff(F.indptr) >= 0)
+        assert np.all(np.diff(S0.indptr) == m0) and np.all(np.diff(S1.indptr) == m0)
+        assert np.all(np.diff(S2.tocsc().indptr) == m2)
+    for F_lo, F_hi in zip(w.levels[0][:2], w.levels[1][:2]):
+        lo = set(zip(*F_lo.nonzero()))
+        assert lo <= set(zip(*F_hi.nonzero()))
+    a = S.meg_faust(n_signals=3, first=2, levels=levels)
+    np.testing.assert_array_equal(a.Y, w.Y[2:5])
+    np.testing.assert_array_equal(a.A, w.A)
+    assert all(len(s) == 8 for s in w.supports)
+    np.testing.assert_allclose(np.linalg.norm(w.Y, axis=1), 1.0, rtol=1e-6)
