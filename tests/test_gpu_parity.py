@@ -54,6 +54,29 @@ def test_lambda_at_or_above_lambda_max_returns_zero(pkg):
     assert np.all(x == 0) and gap == 0.0
 
 
+def test_empty_batch_and_oversized_signals_are_rejected(pkg):
+    """Host-side rejections before any device work: an empty batch (LASSO_ERR_INVALID_ARG) and
+    signals longer than the supported 24576 padded entries (LASSO_ERR_UNSUPPORTED).  The
+    dictionary stays usable after a rejected call."""
+    w = S.dense_small(N=64, K=256, n_signals=2, seed=1)
+    d = pkg.Dictionary.dense(w.A, dtype="f32")
+    Y = torch.tensor(w.Y, dtype=torch.float32, device="cuda")
+    ratios = torch.tensor(w.lam_ratio, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.LassoError) as e:
+        d.solve_batch(Y[:0].contiguous(), ratios[:0].contiguous(), 1e-6, lambda_relative=1)
+    assert e.value.code == -1
+    X, gaps, status, iters, st = d.solve_batch(Y, ratios, 1e-6, lambda_relative=1)
+    assert bool((status == 0).all()) and float(gaps.max()) <= 1e-6
+    d.close()
+    rng = np.random.default_rng(0)
+    db = pkg.Dictionary.dense(rng.standard_normal((24577, 8)).astype(np.float32), dtype="f32", normalize=True)
+    Yb = torch.tensor(rng.standard_normal((1, 24577)), dtype=torch.float32, device="cuda")
+    with pytest.raises(pkg.LassoError) as e:
+        db.solve_batch(Yb, torch.tensor([0.5], dtype=torch.float64, device="cuda"), 1e-6, lambda_relative=1)
+    assert e.value.code == -6
+    db.close()
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_brute_force_small_fp64(pkg, seed):
     r = np.random.default_rng(70 + seed)
