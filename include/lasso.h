@@ -61,7 +61,8 @@ typedef enum {
 
 typedef struct lasso_dict lasso_dict;
 
-/* Create a dense dictionary (the exact A of the problem).  dt gives the element type of A and
+/* Create a dense dictionary: the exact A of the problem min_x 1/2 ||y - A x||^2 + lambda ||x||_1
+ * (eq:lasso; atoms are the columns a_j).  dt gives the element type of A and
  * the precision of the exact level (FP64 data: FP64 arithmetic; FP32 data: FP32 products with
  * compensated accumulation).  normalize != 0 rescales every atom to unit l2 norm first (in
  * FP64, then rounded to dt); the problem solved is then the one with normalised atoms.
@@ -69,12 +70,16 @@ typedef struct lasso_dict lasso_dict;
 int lasso_dict_create_dense(const void* A, lasso_dtype dt, int64_t N, int64_t K, int64_t ld,
                             int atom_major, int normalize, int host_ptr, lasso_dict** out);
 
-/* Create a sum-of-Kronecker dictionary (SuKro, Section V-A) from its factors (FP32, host or
- * device).  The exact A is the FP64 Kronecker sum with unit atoms; the library stores a dense
- * FP32 rounding of it as the last level (its rounding error enters eps_j), and the structured
- * truncations are added with lasso_dict_add_level(LASSO_LEVEL_KRON, R'). */
+/* Create a sum-of-Kronecker dictionary (SuKro, Section V-A: A = sum_r B_r (x) C_r) from its
+ * factors (FP32, host memory if host_ptr != 0, else device memory; the library copies them).
+ * B holds R row-major N1 x K1 factors, C holds R row-major N2 x K2 factors.  The exact A is the
+ * FP64 Kronecker sum times diag(d): normalize != 0 gives unit atoms (d_j = 1 / ||column j||,
+ * computed in FP64), normalize == 0 keeps the sum as given (d_j = 1).  The library stores a
+ * dense FP32 rounding of A as the last level (its rounding error enters eps_j), and the
+ * structured truncations are added with lasso_dict_add_level(LASSO_LEVEL_KRON, R').
+ * Returns LASSO_ERR_INVALID_ARG for null factors, a non-positive size or R > 64 (*out = NULL). */
 int lasso_dict_create_kron(const float* B, const float* C, int R, int N1, int K1, int N2, int K2,
-                           int host_ptr, lasso_dict** out);
+                           int normalize, int host_ptr, lasso_dict** out);
 
 /* Append an approximate dictionary below the exact one.  Levels must be added from the
  * coarsest to the finest; the exact dictionary always stays last (A~^I = A).  eps_j is
@@ -176,6 +181,13 @@ typedef struct {
                                 of 64 / 128 / 256 and 4 / 8 / 16 blocks per SM on a synthetic
                                 exact-level state (K / 8 preserved atoms per signal) and keep the
                                 fastest for the dictionary; 0: 128-atom chunks, 8 blocks per SM */
+    uint8_t* kept_mask;      /* optional output of the batch calls (default NULL): B x K bytes, row b
+                                = signal b, 1 where atom j is in the signal's preserved set at exit
+                                and 0 where a safe test rejected it (Definition 2: a rejected atom
+                                is zero in every solution).  Device memory for lasso_solve_batch,
+                                host memory for lasso_solve_batch_host; ignored by lasso_solve,
+                                which returns its preserved set as a sorted list.  A signal with
+                                lambda >= lambda_max, or y = 0, has an empty set.               */
 } lasso_opts;
 
 /* Fill *opts with the defaults above. */
@@ -202,7 +214,9 @@ typedef struct {
     int64_t corr_blocks_per_sm; /* correlation grid, in blocks per SM                           */
 } lasso_stats;
 
-/* Solve one signal (host buffers).  y: N values (rounded to the exact level's precision on
+/* Solve one signal with FastL1 (Algorithm 1: FISTA / ISTA on the preserved atoms, stable safe
+ * screening, SwitchDictionary of Algorithm 2 along the ladder) to the relative gap tol.  Host
+ * buffers.  y: N values (rounded to the exact level's precision on
  * entry).  lambda: absolute, or relative to lambda_max if opts->lambda_relative.  Outputs:
  * x_host (K, zero outside the preserved set), gap_host (relative gap of the returned point),
  * kept_host (capacity K, sorted preserved set at exit, may be NULL), n_kept (may be NULL),
@@ -211,33 +225,53 @@ int lasso_solve(lasso_dict* dict, const double* y_host, double lambda, double to
                 const lasso_opts* opts, double* x_host, double* gap_host, int32_t* kept_host,
                 int64_t* n_kept, lasso_stats* stats);
 
-/* Solve B signals in one batch on `stream` (a cudaStream_t, NULL = default stream).  Device
+/* Solve B independent signals with Algorithm 1 in one batch on `stream` (a cudaStream_t, NULL =
+ * default stream); each signal has its own lambda, preserved set and ladder level.  Device
  * buffers: d_Y (B x N FP32, row b = y_b), d_lambdas (B FP64), d_X (B x K FP32 output),
  * d_gaps (B FP64 output), d_status (B int32 output: lasso_status per signal), d_iters (B int32
- * output, may be NULL).  Synchronises the stream before returning. */
+ * output, may be NULL); opts->kept_mask optionally receives the preserved sets.
+ * Synchronisation: the passes run as a CUDA graph of opts->passes_per_sync passes, replayed
+ * until every signal has stopped; between replays the host reads a 4-byte count of finished
+ * signals from the device (one stream synchronisation per replay), and the stream is
+ * synchronised before the call returns.  The FP64 second solve of saturated signals
+ * (opts->fp64_fallback) allocates and frees its own buffers.
+ * Per-signal status: LASSO_OK, LASSO_ERR_MAXITER (pass limit), LASSO_ERR_TIMEOUT (the call's
+ * wall-clock limit; every live signal stops at its next pass), LASSO_ERR_NONFINITE (NaN / Inf
+ * in y_b or in its gap), LASSO_ERR_INVALID_ARG (lambda_b not positive and finite).  On
+ * MAXITER and TIMEOUT, row b of d_X is the signal's current point and d_gaps[b] the certificate
+ * evaluated at it (the relative gap of the reduced problem).  The call returns
+ * LASSO_ERR_TIMEOUT when the wall-clock limit stopped it, else LASSO_OK once every signal has
+ * a status (per-signal errors are reported in d_status only), or a call-level error. */
 int lasso_solve_batch(lasso_dict* dict, const float* d_Y, const double* d_lambdas, int64_t B,
                       double tol, const lasso_opts* opts, float* d_X, double* d_gaps,
                       int32_t* d_status, int32_t* d_iters, void* stream, lasso_stats* stats);
 
-/* Same with host buffers: copies inputs to the device, solves, copies results back. */
+/* Same with host buffers (opts->kept_mask, if set, is host memory too): copies inputs to the
+ * device, solves (Algorithm 1), copies results back. */
 int lasso_solve_batch_host(lasso_dict* dict, const float* Y_host, const double* lambdas_host,
                            int64_t B, double tol, const lasso_opts* opts, float* X_host,
                            double* gaps_host, int32_t* status_host, lasso_stats* stats);
 
-/* lambda_max = ||A^T y||_inf of B signals (device buffers, exact level, FP64 output). */
+/* lambda_max = ||A^T y||_inf of B signals (eq:DefLMax: for lambda >= lambda_max the solution is
+ * x = 0).  Device buffers: d_Y (B x N FP32), d_out (B FP64 output); exact level, error-free
+ * products; queued on `stream` (a cudaStream_t).  May allocate its workspace on first use. */
 int lasso_lambda_max(lasso_dict* dict, const float* d_Y, int64_t B, double* d_out, void* stream);
 
 /* Same values as lasso_lambda_max, for callers that cannot allocate device memory (their
  * device memory belongs to another allocator, or they cannot afford cudaMalloc's implicit
  * synchronisation).  The paper has no counterpart: this is a deployment variant.
- * It allocates nothing: its scratch is a fixed 8 MiB array inside the library (1048576
- * doubles, held by every GPU that loads the library until the process exits), so it needs
- * B * ceil(K / 256) <= 1048576 and B <= 65535, else it returns LASSO_ERR_UNSUPPORTED.
- * Device buffers: d_Y (B x N FP32), d_out (B FP64).  The work is queued on `stream` (a
- * cudaStream_t; the call does not wait for it).  The first call on each device looks up the
- * scratch address with that device current; make that first call before any stream capture.
- * Every call shares the one scratch array: calls whose work overlaps on the GPU (other
- * streams, other threads) race and must be serialised by the caller. */
+ * It allocates nothing, not even on its first call for a dictionary: its scratch is a fixed
+ * 8 MiB array inside the library (1048576 doubles, held by every GPU that loads the library
+ * until the process exits), and it reads only the exact level's atom rows.  Limits, each
+ * returning LASSO_ERR_UNSUPPORTED with a message: B * ceil(K / 256) <= 1048576, B <= 65535,
+ * and the padded signal must fit the 200 KiB of shared memory it is staged in (N <= 51200 for
+ * FP32 dictionaries, N <= 25600 for FP64).  The dictionary's device must be the current CUDA
+ * device (else LASSO_ERR_INVALID_ARG).
+ * Device buffers: d_Y (B x N FP32, rows contiguous), d_out (B FP64).  The work is queued on
+ * `stream` (a cudaStream_t; the call does not wait for it).  The first call on each device
+ * looks up the scratch address with that device current; make that first call before any
+ * stream capture.  Every call shares the one scratch array: calls whose work overlaps on the
+ * GPU (other streams, other threads) race and must be serialised by the caller. */
 int lasso_lambda_max_noalloc(const lasso_dict* dict, const float* d_Y, int64_t B, double* d_out,
                              void* stream);
 
@@ -250,7 +284,8 @@ int lasso_lambda_max_noalloc(const lasso_dict* dict, const float* d_Y, int64_t B
 int lasso_backward(lasso_dict* dict, const float* d_Y, const float* d_X, const float* d_G,
                    int64_t B, float* d_dY, float* d_dA, void* stream);
 
-/* Check of the tensor-core GEMM behind the batched BF16 / FP8 levels and the split exact level:
+/* DIAGNOSTIC, not part of the solve path.
+ * Check of the tensor-core GEMM behind the batched BF16 / FP8 levels and the split exact level:
  * B x K correlations of random operands (N terms each; signed values, and all-positive values
  * for the worst accumulation) through tcgen05, compared with an FP64 evaluation of the same
  * products.  max_rel_err: largest |error| / sum_i |a_i r_i|; max_err_over_bound: largest |error|
@@ -261,7 +296,8 @@ int lasso_backward(lasso_dict* dict, const float* d_Y, const float* d_X, const f
  * rounding model (products treated as exact there). */
 int lasso_tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel_err, double* max_err_over_bound);
 
-/* Read bandwidth (GB/s) of a buffer resident in L2 (bytes in [1 MiB, 96 MiB]), read `rounds`
+/* DIAGNOSTIC, not part of the solve path (the benchmark's roofline denominator).
+ * Read bandwidth (GB/s) of a buffer resident in L2 (bytes in [1 MiB, 96 MiB]), read `rounds`
  * times by one launch with 16-byte loads that bypass L1; the roofline denominator of kernels
  * whose operands stay in L2 across a batch.  The paper has no counterpart (hardware
  * measurement).  Allocates and frees its buffer; synchronises the device. */

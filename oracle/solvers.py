@@ -9,7 +9,7 @@ then the switch.  With a single exact level it is plain FISTA + GAP Safe screeni
 reference solution used for parity).  ``kkt_polish`` and ``brute_force`` compute the
 minimiser without iterating, for pins and for exact reference values.
 
-Readings of points the paper leaves open (each also listed in the design notes):
+Readings of points the paper leaves open:
 * FISTA recursion (cited, never written): t_0 = 1, t+ = (1 + sqrt(1 + 4 t^2)) / 2,
   z+ = x+ + ((t - 1) / t+)(x+ - x); momentum kept across dictionary switches; a rejected
   coordinate is zeroed in x and z.

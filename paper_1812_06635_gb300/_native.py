@@ -31,6 +31,7 @@ class LassoOpts(C.Structure):
         ("tc_exact", C.c_int),
         ("fp64_fallback", C.c_int),
         ("autotune", C.c_int),
+        ("kept_mask", C.c_void_p),
     ]
 
 
@@ -75,7 +76,8 @@ PD = C.POINTER(C.c_double)
 # (name, restype, argtypes) for every function of include/lasso.h
 SIGNATURES = [
     ("lasso_dict_create_dense", C.c_int, [P, C.c_int, I64, I64, I64, C.c_int, C.c_int, C.c_int, C.POINTER(P)]),
-    ("lasso_dict_create_kron", C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(P)]),
+    ("lasso_dict_create_kron", C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                         C.POINTER(P)]),
     ("lasso_dict_add_level", C.c_int, [P, C.c_int, C.c_int]),
     ("lasso_dict_add_level_faust", C.c_int, [P, C.c_int, P, P, P, P]),
     ("lasso_dict_set_rc", C.c_int, [P, C.c_int, C.c_double]),

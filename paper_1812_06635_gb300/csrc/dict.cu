@@ -188,15 +188,24 @@ __device__ __forceinline__ double kron_gram_sum(const double* GB, const double* 
 }
 
 // d_j = 1 / ||(sum_r B_r (x) C_r) e_j|| (FP64, Gram identity).
+// Column scale d_j of A = (sum_r B_r (x) C_r) diag(d): 1 / ||column j|| (unit atoms) when
+// normalize != 0, else 1 (the Kronecker sum as given); anorm_j >= ||a_j|| in both cases.
 __global__ void k_kron_scale(const double* __restrict__ GB, const double* __restrict__ GC, int R, int K1, int K2,
-                             double* __restrict__ d, float* __restrict__ df, double* __restrict__ anorm) {
+                             int normalize, double* __restrict__ d, float* __restrict__ df, double* __restrict__ anorm) {
   int K = K1 * K2;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
     double sq = kron_gram_sum(GB, GC, R, K1, K2, j / K2, j % K2, 0, R);
-    double dj = sq > 0.0 ? 1.0 / sqrt(sq) : 0.0;
-    d[j] = dj;
-    df[j] = (float)dj;
-    anorm[j] = 1.0 + 1e-12;   // unit atoms (FP64 rounding of d_j covered by the slack)
+    if (normalize) {
+      double dj = sq > 0.0 ? 1.0 / sqrt(sq) : 0.0;
+      d[j] = dj;
+      df[j] = (float)dj;
+      anorm[j] = 1.0 + 1e-12;   // unit atoms (FP64 rounding of d_j covered by the slack)
+    } else {
+      d[j] = 1.0;
+      df[j] = 1.0f;
+      // the Gram sum of 2 R^2 terms, then a square root: relative error far below 1e-12
+      anorm[j] = sqrt(fmax(sq, 0.0)) * (1.0 + 1e-12);
+    }
   }
 }
 
@@ -963,7 +972,7 @@ fail:
 }
 
 extern "C" int lasso_dict_create_kron(const float* B, const float* C, int R, int N1, int K1, int N2, int K2,
-                                      int host_ptr, lasso_dict** out) {
+                                      int normalize, int host_ptr, lasso_dict** out) {
   if (!out) return LASSO_ERR_INVALID_ARG;
   *out = nullptr;
   if (!B || !C || R <= 0 || N1 <= 0 || K1 <= 0 || N2 <= 0 || K2 <= 0 || R > 64) return LASSO_ERR_INVALID_ARG;
@@ -996,7 +1005,7 @@ extern "C" int lasso_dict_create_kron(const float* B, const float* C, int R, int
   if ((rc = alloc((void**)&d->anorm, d->K * 8))) goto fail;
   k_kron_gram<<<grid_for((int64_t)R * R * K1), 256>>>(d->Bf, R, N1, K1, d->gramB);
   k_kron_gram<<<grid_for((int64_t)R * R * K2), 256>>>(d->Cf, R, N2, K2, d->gramC);
-  k_kron_scale<<<grid_for(d->K), 256>>>(d->gramB, d->gramC, R, K1, K2, d->d, dfl, d->anorm);
+  k_kron_scale<<<grid_for(d->K), 256>>>(d->gramB, d->gramC, R, K1, K2, normalize, d->d, dfl, d->anorm);
   {
     HostLevel& h = d->exact;
     h.kind = LK_F32;

@@ -10,6 +10,7 @@
 // The scratch is one file-scope __device__ array (every GPU that loads the library keeps it
 // until the process exits).  Host code cannot use the array's name as a device address, so
 // the address is looked up once per device with cudaGetSymbolAddress and cached.
+#include <cstring>
 #include <mutex>
 
 #include "dict.cuh"
@@ -22,6 +23,7 @@ constexpr int64_t NOALLOC_SCRATCH_DOUBLES = 1 << 20;   // 8 MiB
 constexpr int NA_ATOMS_PER_BLOCK = 256;
 constexpr int NA_THREADS = 256;
 constexpr int NA_MAX_DEVICES = 64;
+constexpr int NA_MAX_SMEM = 200 * 1024;    // y_b staged in shared memory
 
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
@@ -74,7 +76,10 @@ static double* g_na_ptr[NA_MAX_DEVICES] = {nullptr};
 static int noalloc_scratch(double** out) {
   int dev = 0;
   LASSO_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= NA_MAX_DEVICES) return LASSO_ERR_UNSUPPORTED;
+  if (dev < 0 || dev >= NA_MAX_DEVICES) {
+    set_last_error("lasso_lambda_max_noalloc: device ordinal above 63", __FILE__, __LINE__);
+    return LASSO_ERR_UNSUPPORTED;
+  }
   std::lock_guard<std::mutex> lock(g_na_mutex);
   if (!g_na_ptr[dev]) {
     void* p = nullptr;
@@ -93,9 +98,36 @@ static int noalloc_scratch(double** out) {
 
 using namespace lasso;
 
+// The exact level as k_noalloc_partial_max reads it.  warp_atom_dot on the exact FP32 / FP64
+// level reads only the kind, the row stride and the atom rows, so the descriptor is filled
+// from the dictionary's own fields: the regular make_level_dev() may create the level's FP32
+// bound arrays on first use, which would allocate and synchronise the device.
+static LevelDev exact_level_rows(const lasso_dict* d) {
+  LevelDev L;
+  memset(&L, 0, sizeof(L));
+  L.kind = d->exact.kind;
+  L.ld = d->ldN;
+  L.data = d->exact.data;
+  return L;
+}
+
 extern "C" int lasso_lambda_max_noalloc(const lasso_dict* d, const float* d_Y, int64_t B, double* d_out,
                                         void* stream) {
-  if (!d || !d_Y || !d_out || B <= 0) return LASSO_ERR_INVALID_ARG;
+  if (!d || !d_Y || !d_out || B <= 0) {
+    set_last_error("lasso_lambda_max_noalloc: null dictionary or buffer, or B <= 0", __FILE__, __LINE__);
+    return LASSO_ERR_INVALID_ARG;
+  }
+  if (!d->exact.data || (d->exact.kind != LK_F32 && d->exact.kind != LK_F64)) {
+    set_last_error("lasso_lambda_max_noalloc: the dictionary has no dense exact level", __FILE__, __LINE__);
+    return LASSO_ERR_INVALID_ARG;
+  }
+  int dev = -1;
+  LASSO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != d->device) {
+    set_last_error("lasso_lambda_max_noalloc: the current CUDA device is not the dictionary's device",
+                   __FILE__, __LINE__);
+    return LASSO_ERR_INVALID_ARG;
+  }
   const int64_t nchunk = (d->K + NA_ATOMS_PER_BLOCK - 1) / NA_ATOMS_PER_BLOCK;
   if (B > 65535 || B * nchunk > NOALLOC_SCRATCH_DOUBLES) {
     set_last_error("lasso_lambda_max_noalloc: B * ceil(K / 256) exceeds the 1048576-entry scratch "
@@ -103,13 +135,18 @@ extern "C" int lasso_lambda_max_noalloc(const lasso_dict* d, const float* d_Y, i
     return LASSO_ERR_UNSUPPORTED;
   }
   const size_t smem = (size_t)d->ldN * (d->exact.kind == LK_F64 ? 8 : 4);
-  if (smem > 200 * 1024) return LASSO_ERR_UNSUPPORTED;
+  if (smem > NA_MAX_SMEM) {
+    set_last_error("lasso_lambda_max_noalloc: the signal (padded length x element size) exceeds the "
+                   "200 KiB of shared memory this kernel stages it in (N <= 51200 for FP32 "
+                   "dictionaries, N <= 25600 for FP64)", __FILE__, __LINE__);
+    return LASSO_ERR_UNSUPPORTED;
+  }
   double* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc) return rc;
-  const LevelDev L = make_level_dev(d, d->exact, d->exact.kind == LK_F64);
+  const LevelDev L = exact_level_rows(d);
   cudaStream_t st = (cudaStream_t)stream;
-  LASSO_CUDA_TRY(cudaFuncSetAttribute(k_noalloc_partial_max, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  LASSO_CUDA_TRY(cudaFuncSetAttribute(k_noalloc_partial_max, cudaFuncAttributeMaxDynamicSharedMemorySize, NA_MAX_SMEM));
   k_noalloc_partial_max<<<dim3((unsigned)nchunk, (unsigned)B), NA_THREADS, smem, st>>>(
       L, (int)d->N, d->ldN, d->K, d_Y, (int)nchunk, scratch);
   k_noalloc_reduce<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(scratch, B, (int)nchunk, d_out);

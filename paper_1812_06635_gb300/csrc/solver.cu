@@ -1076,8 +1076,10 @@ __device__ void pass_decide(SigState& s, const PassArgs<VT>& a, double m1_bulk, 
     // with the rejected atoms are checked (full-dictionary gap, stopping rule of Section IV)
     s.pending = 1;
     s.snap = 1;
-  } else if (s.iters >= a.sp.max_iter) {
-    s.status = LASSO_ERR_MAXITER;
+  } else if (s.iters >= a.sp.max_iter || a.counters[1]) {
+    // pass limit, or the host's wall-clock limit (counters[1]): stop with the current point
+    // and its certificate (partial x, last certified gap)
+    s.status = a.counters[1] ? LASSO_ERR_TIMEOUT : LASSO_ERR_MAXITER;
     action = 2;
   }
   if (s.level == I || action) s.gap = gcert;
@@ -2089,13 +2091,21 @@ __global__ void k_cert_finish(PassArgs<VT> a) {
 
 template <typename VT>
 __global__ void k_outputs(PassArgs<VT> a, float* __restrict__ Xf, double* __restrict__ gaps, int32_t* __restrict__ status,
-                          int32_t* __restrict__ iters) {
+                          int32_t* __restrict__ iters, uint8_t* __restrict__ kept_out) {
   const int b = blockIdx.y;
   const SigState& s = a.st[b];
   if (Xf) {
     const VT* xo = a.Xout + (int64_t)b * a.K;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.K; j += (int64_t)gridDim.x * blockDim.x)
       Xf[(int64_t)b * a.K + j] = (float)xo[j];
+  }
+  if (kept_out) {
+    // the preservation mask is cleared by every rejection; an empty preserved set (lambda >=
+    // lambda_max, y = 0) leaves it untouched, hence the n_kept test
+    const uint8_t* mk = a.mask + (int64_t)b * a.K;
+    const bool any = s.n_kept > 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.K; j += (int64_t)gridDim.x * blockDim.x)
+      kept_out[(int64_t)b * a.K + j] = any ? mk[j] : (uint8_t)0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (gaps) gaps[b] = s.gap;
@@ -2493,7 +2503,9 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   }
   int64_t replays = 0;
   int result = LASSO_OK;
+  bool timed_out = false;
   const int64_t max_replays = (int64_t)pa.sp.max_iter / k + 2;
+  LASSO_CUDA_TRY(cudaMemsetAsync(w->counters + 1, 0, 4, st));   // wall-clock stop flag
   while (true) {
     ce = cudaMemcpyAsync(w->h_counters, w->counters, 4, cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
@@ -2517,12 +2529,20 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
       cudaGetLastError();   // a failed timing query must not leave a sticky error behind
     }
     if (w->h_counters[0] >= B) break;
-    if (replays >= max_replays) break;
+    if (replays >= max_replays || timed_out) break;
     if (o.time_limit_s > 0.0) {
       double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
       if (el > o.time_limit_s) {
+        // one more replay: every live signal takes the flag at its next pass and stops with its
+        // current point and certificate (status LASSO_ERR_TIMEOUT)
         result = LASSO_ERR_TIMEOUT;
-        break;
+        timed_out = true;
+        ce = cudaMemsetAsync(w->counters + 1, 1, 1, st);
+        if (ce != cudaSuccess) {
+          set_last_error(cudaGetErrorString(ce), __FILE__, __LINE__);
+          result = LASSO_ERR_CUDA;
+          break;
+        }
       }
     }
     ce = cudaGraphLaunch(exec, st);
@@ -2561,7 +2581,8 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     launches += 2;
   }
   launches += 1;
-  k_outputs<VT><<<dim3(io.Xf ? 64 : 1, (unsigned)B), 256, 0, st>>>(pa, io.Xf, io.gaps, io.status, io.iters);
+  k_outputs<VT><<<dim3(io.Xf || io.opts.kept_mask ? 64 : 1, (unsigned)B), 256, 0, st>>>(pa, io.Xf, io.gaps, io.status,
+                                                                                       io.iters, io.opts.kept_mask);
   LASSO_CUDA_TRY(cudaGetLastError());
   LASSO_CUDA_TRY(cudaStreamSynchronize(st));
   if (stats) {
@@ -2642,13 +2663,16 @@ __global__ void k_gather_saturated(const SigState* __restrict__ st, const float*
 
 __global__ void k_scatter_saturated(const int32_t* __restrict__ idx, int n, int64_t K, const float* __restrict__ Xs,
                                     const double* __restrict__ gs, const int32_t* __restrict__ ss,
-                                    const int32_t* __restrict__ is, float* __restrict__ X, double* __restrict__ gaps,
-                                    int32_t* __restrict__ status, int32_t* __restrict__ iters) {
+                                    const int32_t* __restrict__ is, const uint8_t* __restrict__ ks,
+                                    float* __restrict__ X, double* __restrict__ gaps,
+                                    int32_t* __restrict__ status, int32_t* __restrict__ iters, uint8_t* __restrict__ kept) {
   const int i = blockIdx.x;
   if (i >= n) return;
   const int64_t b = idx[i];
   if (X)
     for (int64_t j = threadIdx.x; j < K; j += blockDim.x) X[b * K + j] = Xs[(int64_t)i * K + j];
+  if (kept && ks)
+    for (int64_t j = threadIdx.x; j < K; j += blockDim.x) kept[b * K + j] = ks[(int64_t)i * K + j];
   if (threadIdx.x == 0) {
     if (gaps) gaps[b] = gs[i];
     if (status) status[b] = ss[i];
@@ -2665,7 +2689,9 @@ static int fp64_fallback(lasso_dict* d, Workspace* w, SolveIO& io, lasso_stats* 
   int32_t *idx = nullptr, *cnt = nullptr, *ss = nullptr, *is = nullptr;
   float *Ys = nullptr, *Xs = nullptr;
   double *lam = nullptr, *gs = nullptr;
+  uint8_t* ks = nullptr;
   auto release = [&]() {
+    cudaFree(ks);
     cudaFree(idx);
     cudaFree(cnt);
     cudaFree(ss);
@@ -2690,7 +2716,8 @@ static int fp64_fallback(lasso_dict* d, Workspace* w, SolveIO& io, lasso_stats* 
   }
   if (cudaMalloc(&Ys, (size_t)n * N * 4) != cudaSuccess || cudaMalloc(&lam, (size_t)n * 8) != cudaSuccess ||
       cudaMalloc(&Xs, (size_t)n * K * 4) != cudaSuccess || cudaMalloc(&gs, (size_t)n * 8) != cudaSuccess ||
-      cudaMalloc(&ss, (size_t)n * 4) != cudaSuccess || cudaMalloc(&is, (size_t)n * 4) != cudaSuccess) {
+      cudaMalloc(&ss, (size_t)n * 4) != cudaSuccess || cudaMalloc(&is, (size_t)n * 4) != cudaSuccess ||
+      (io.opts.kept_mask && cudaMalloc(&ks, (size_t)n * K) != cudaSuccess)) {
     release();
     return LASSO_ERR_NOMEM;
   }
@@ -2710,10 +2737,12 @@ static int fp64_fallback(lasso_dict* d, Workspace* w, SolveIO& io, lasso_stats* 
   sub.gaps = gs;
   sub.status = ss;
   sub.iters = is;
+  sub.opts.kept_mask = ks;
   lasso_stats sst;
   const int rc = solve_common(d, sub, stats ? &sst : nullptr);
   if (rc == LASSO_OK) {
-    k_scatter_saturated<<<n, 256, 0, st>>>(idx, n, K, Xs, gs, ss, is, io.Xf, io.gaps, io.status, io.iters);
+    k_scatter_saturated<<<n, 256, 0, st>>>(idx, n, K, Xs, gs, ss, is, ks, io.Xf, io.gaps, io.status, io.iters,
+                                           io.opts.kept_mask);
     cudaError_t ce = cudaGetLastError();
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) {
@@ -2784,23 +2813,31 @@ extern "C" int lasso_solve_batch_host(lasso_dict* d, const float* Y, const doubl
   float *dY = nullptr, *dX = nullptr;
   double *dl = nullptr, *dg = nullptr;
   int32_t* ds = nullptr;
+  uint8_t* dk = nullptr;
+  lasso_opts o;
+  if (opts) o = *opts;
+  else lasso_opts_default(&o);
+  uint8_t* kept_host = o.kept_mask;
   const size_t BN = (size_t)B * d->N, BK = (size_t)B * d->K;
   int rc = LASSO_OK;
   if (cudaMalloc(&dY, BN * 4) != cudaSuccess || cudaMalloc(&dX, BK * 4) != cudaSuccess ||
       cudaMalloc(&dl, B * 8) != cudaSuccess || cudaMalloc(&dg, B * 8) != cudaSuccess ||
-      cudaMalloc(&ds, B * 4) != cudaSuccess) {
+      cudaMalloc(&ds, B * 4) != cudaSuccess || (kept_host && cudaMalloc(&dk, BK) != cudaSuccess)) {
     rc = LASSO_ERR_NOMEM;
   }
+  o.kept_mask = dk;
   if (!rc && (cudaMemcpy(dY, Y, BN * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
               cudaMemcpy(dl, lambdas, B * 8, cudaMemcpyHostToDevice) != cudaSuccess))
     rc = LASSO_ERR_CUDA;
-  if (!rc) rc = lasso_solve_batch(d, dY, dl, B, tol, opts, dX, dg, ds, nullptr, nullptr, stats);
+  if (!rc) rc = lasso_solve_batch(d, dY, dl, B, tol, &o, dX, dg, ds, nullptr, nullptr, stats);
   if (rc == LASSO_OK || rc == LASSO_ERR_MAXITER || rc == LASSO_ERR_TIMEOUT) {
     if (cudaMemcpy(X, dX, BK * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
         (gaps && cudaMemcpy(gaps, dg, B * 8, cudaMemcpyDeviceToHost) != cudaSuccess) ||
-        (status && cudaMemcpy(status, ds, B * 4, cudaMemcpyDeviceToHost) != cudaSuccess))
+        (status && cudaMemcpy(status, ds, B * 4, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (kept_host && cudaMemcpy(kept_host, dk, BK, cudaMemcpyDeviceToHost) != cudaSuccess))
       rc = LASSO_ERR_CUDA;
   }
+  cudaFree(dk);
   cudaFree(dY);
   cudaFree(dX);
   cudaFree(dl);
@@ -2826,6 +2863,7 @@ extern "C" int lasso_solve(lasso_dict* d, const double* y, double lambda, double
   io.tol = tol;
   if (opts) io.opts = *opts;
   else lasso_opts_default(&io.opts);
+  io.opts.kept_mask = nullptr;   // the single solve returns its preserved set as a list
   lasso_stats local;
   int rc = solve_common(d, io, stats ? stats : &local);
   cudaFree(dy);

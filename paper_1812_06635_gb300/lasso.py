@@ -65,6 +65,26 @@ def _ptr(a) -> C.c_void_p:
     return C.c_void_p(a.ctypes.data)
 
 
+def noalloc_args(Y, out, N: int, device_type: str = "cuda"):
+    """Validate the buffers of ``lasso_lambda_max_noalloc`` and return ``out`` (allocated when None).
+
+    Y must be a contiguous float32 tensor of shape (B > 0, N) on a ``device_type`` device; out,
+    when given, a contiguous float64 tensor of at least B entries on Y's device.  Raises
+    ValueError otherwise.  ``device_type`` is "cuda" for real calls (host tests pass "cpu").
+    """
+    import torch
+    if not (isinstance(Y, torch.Tensor) and Y.device.type == device_type and Y.dtype == torch.float32
+            and Y.dim() == 2 and Y.is_contiguous() and Y.shape[1] == N and Y.shape[0] > 0):
+        raise ValueError(f"Y must be a contiguous {device_type} float32 tensor of shape (B > 0, {N})")
+    B = Y.shape[0]
+    if out is None:
+        return torch.empty(B, dtype=torch.float64, device=Y.device)
+    if not (isinstance(out, torch.Tensor) and out.dtype == torch.float64 and out.is_contiguous()
+            and out.numel() >= B and out.device == Y.device):
+        raise ValueError(f"out must be a contiguous float64 tensor of at least {B} entries on {Y.device}")
+    return out
+
+
 class Dictionary:
     """A dictionary (exact A) and its ladder of approximations, owned by the library."""
 
@@ -95,15 +115,17 @@ class Dictionary:
         return cls(h, N, K)
 
     @classmethod
-    def kron(cls, Bf, Cf) -> "Dictionary":
-        """A = (sum_r B_r (x) C_r) diag(d), unit atoms; Bf: R x N1 x K1, Cf: R x N2 x K2."""
+    def kron(cls, Bf, Cf, normalize: bool = True) -> "Dictionary":
+        """A = (sum_r B_r (x) C_r) diag(d); Bf: R x N1 x K1, Cf: R x N2 x K2.  d_j makes the atoms
+        unit-norm when ``normalize`` (the default), else d = 1 (the Kronecker sum as given)."""
         lib = nat.load()
         Bf = np.ascontiguousarray(np.asarray(Bf, dtype=np.float32))
         Cf = np.ascontiguousarray(np.asarray(Cf, dtype=np.float32))
         R, N1, K1 = Bf.shape
         _, N2, K2 = Cf.shape
         h = C.c_void_p()
-        nat.check(lib.lasso_dict_create_kron(_ptr(Bf), _ptr(Cf), R, N1, K1, N2, K2, 1, C.byref(h)),
+        nat.check(lib.lasso_dict_create_kron(_ptr(Bf), _ptr(Cf), R, N1, K1, N2, K2, int(normalize), 1,
+                                             C.byref(h)),
                   "lasso_dict_create_kron")
         return cls(h, N1 * N2, K1 * K2)
 
@@ -176,15 +198,22 @@ class Dictionary:
         nat.check(code, "lasso_solve", ok=(0, 1))
         return x, gap.value, kept[: nk.value].copy(), Stats.of(st)
 
-    def solve_batch(self, Y, lambdas, tol: float = 1e-6, stream=None, **opts):
+    def solve_batch(self, Y, lambdas, tol: float = 1e-6, stream=None, kept=None, **opts):
         """Batch on the device.  Y: torch CUDA float32 (B x N); lambdas: torch CUDA float64 (B,).
 
         Returns (X (B x K float32), gaps (B float64), status (B int32), iters (B int32), Stats).
+        ``kept``: optional CUDA uint8 tensor (B x K, contiguous) that receives the preserved sets
+        at exit (1 = preserved, 0 = rejected by a safe test).
         """
         import torch
         lib = nat.load()
         assert Y.is_cuda and Y.dtype == torch.float32 and Y.is_contiguous()
         B = Y.shape[0]
+        if kept is not None:
+            if not (kept.is_cuda and kept.dtype == torch.uint8 and kept.is_contiguous()
+                    and tuple(kept.shape) == (B, self.K) and kept.device == Y.device):
+                raise ValueError(f"kept must be a contiguous CUDA uint8 tensor of shape ({B}, {self.K})")
+            opts["kept_mask"] = kept.data_ptr()
         lam = lambdas.to(device=Y.device, dtype=torch.float64).contiguous()
         X = torch.empty((B, self.K), dtype=torch.float32, device=Y.device)
         gaps = torch.empty(B, dtype=torch.float64, device=Y.device)
@@ -198,12 +227,18 @@ class Dictionary:
         nat.check(code, "lasso_solve_batch", ok=(0, -4, -5))
         return X, gaps, status, iters, Stats.of(st)
 
-    def solve_batch_host(self, Y, lambdas, tol: float = 1e-6, **opts):
-        """Batch with host buffers (the library copies in and out)."""
+    def solve_batch_host(self, Y, lambdas, tol: float = 1e-6, kept=None, **opts):
+        """Batch with host buffers (the library copies in and out).  ``kept``: optional numpy
+        uint8 array (B x K, C-contiguous) that receives the preserved sets at exit."""
         lib = nat.load()
         Y = np.ascontiguousarray(np.asarray(Y, dtype=np.float32))
         lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
         B = Y.shape[0]
+        if kept is not None:
+            if not (isinstance(kept, np.ndarray) and kept.dtype == np.uint8 and kept.flags.c_contiguous
+                    and kept.shape == (B, self.K)):
+                raise ValueError(f"kept must be a C-contiguous numpy uint8 array of shape ({B}, {self.K})")
+            opts["kept_mask"] = kept.ctypes.data
         X = np.zeros((B, self.K), dtype=np.float32)
         gaps = np.zeros(B)
         status = np.zeros(B, dtype=np.int32)
@@ -224,14 +259,18 @@ class Dictionary:
         return out
 
     def lambda_max_noalloc(self, Y, out=None):
-        """lambda_max through the allocation-free entry point; ``out`` (B float64) may be given."""
+        """lambda_max through the allocation-free entry point; ``out`` (B float64) may be given.
+
+        The kernel reads B x N floats from ``Y`` and writes B doubles to ``out`` by raw device
+        pointer, so both are checked first (``noalloc_args``): a wrong dtype, shape, layout or
+        device would otherwise make it read or write outside the tensors.
+        """
         import torch
-        B = Y.shape[0]
-        if out is None:
-            out = torch.empty(B, dtype=torch.float64, device=Y.device)
+        out = noalloc_args(Y, out, self.N)
         s = torch.cuda.current_stream(Y.device)
-        nat.check(nat.load().lasso_lambda_max_noalloc(self._h, _ptr(Y), B, _ptr(out), C.c_void_p(s.cuda_stream)),
-                  "lasso_lambda_max_noalloc")
+        with torch.cuda.device(Y.device):
+            nat.check(nat.load().lasso_lambda_max_noalloc(self._h, _ptr(Y), Y.shape[0], _ptr(out),
+                                                          C.c_void_p(s.cuda_stream)), "lasso_lambda_max_noalloc")
         return out
 
     def backward(self, Y, X, G, want_dA: bool = True):
@@ -260,6 +299,13 @@ def _autograd():
         @staticmethod
         def forward(ctx, Y, A, dictionary, lambdas, tol, opts):
             X, gaps, status, iters, _ = dictionary.solve_batch(Y.contiguous(), lambdas, tol, **(opts or {}))
+            bad = torch.nonzero(status != 0).flatten()
+            if bad.numel():
+                # a signal that stopped on the pass limit, the time limit or a non-finite value
+                # holds a partial point: the support adjoint would not be the minimiser's derivative
+                b = int(bad[0])
+                raise nat.LassoError(int(status[b]), f"LassoFn.forward: {bad.numel()} signal(s) not solved to tol "
+                                                     f"(first: signal {b})")
             ctx.dictionary = dictionary
             ctx.want_dA = A is not None and A.requires_grad
             ctx.save_for_backward(Y, X)

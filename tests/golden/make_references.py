@@ -2,7 +2,7 @@
 
     python tests/golden/make_references.py [c3|meg_faust]   (both when no name is given)
 
-c3_reference.npz: for a few signals of the c3 batch (2048 x 8192, seed 0) the Lasso minimiser at
+c3_reference.npz: for 20 signals of the c3 batch (2048 x 8192, seed 0) the Lasso minimiser at
 lambda = ratio * lambda_max, computed by the FP64 oracle (FISTA + GAP Safe, then the KKT-verified
 support system), stored sparsely (support, values), with lambda_max and lambda.
 meg_faust_reference.npz: the same for sampled signals of the source-localisation stand-in
@@ -20,7 +20,11 @@ import synthetic as S                      # noqa: E402
 from oracle import lasso as OL             # noqa: E402
 from oracle import solvers as OS           # noqa: E402
 
-C3_SIGNALS = (0, 1, 2, 4095)
+# c3 signals compared element by element: the first ones, the four smallest and four largest
+# lambda / lambda_max, the three densest and two sparsest x0, one in the middle and the ragged
+# end of the batch (chosen from the generator's draws for seed 0)
+C3_SIGNALS = (0, 1, 2, 15, 315, 1771, 2048, 2084, 2187, 2284, 2298, 3235, 3328, 3513, 3610, 3670, 3810,
+              4093, 4094, 4095)
 MEG_SIGNALS = (0, 23, 49)
 
 

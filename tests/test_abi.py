@@ -43,7 +43,7 @@ def test_host_only_calls(lib):
     # argument validation happens before any device call
     h = C.c_void_p()
     assert lib.lasso_dict_create_dense(None, 1, 10, 10, 10, 1, 0, 1, C.byref(h)) == -1
-    assert lib.lasso_dict_create_kron(None, None, 1, 2, 2, 2, 2, 1, C.byref(h)) == -1
+    assert lib.lasso_dict_create_kron(None, None, 1, 2, 2, 2, 2, 1, 1, C.byref(h)) == -1
     assert lib.lasso_dict_add_level(None, 2, 0) == -1
     assert lib.lasso_dict_add_level_faust(None, 1, None, None, None, None) == -1
     assert lib.lasso_solve(None, None, 1.0, 1e-6, None, None, None, None, None, None) == -1
@@ -52,3 +52,28 @@ def test_host_only_calls(lib):
 def test_library_is_built_for_sm_103a_only():
     from paper_1812_06635_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_noalloc_buffer_checks_reject_bad_tensors():
+    """The allocation-free lambda_max writes through raw pointers, so the binding refuses any
+    buffer whose dtype, shape, layout or device does not match before calling the library
+    (checked here on host tensors; the same function guards the CUDA call)."""
+    torch = pytest.importorskip("torch")
+    from paper_1812_06635_gb300.lasso import noalloc_args
+    N = 8
+    Y = torch.zeros((3, N), dtype=torch.float32)
+    out = noalloc_args(Y, None, N, device_type="cpu")
+    assert out.dtype == torch.float64 and out.numel() == 3
+    assert noalloc_args(Y, torch.zeros(5, dtype=torch.float64), N, device_type="cpu").numel() == 5
+    bad_Y = [Y.double(), torch.zeros((3, N + 1)), torch.zeros((0, N)), torch.zeros(N),
+             torch.zeros((N, 3)).t(), Y.numpy()]
+    for b in bad_Y:
+        with pytest.raises(ValueError):
+            noalloc_args(b, None, N, device_type="cpu")
+    with pytest.raises(ValueError):
+        noalloc_args(Y, None, N, device_type="cuda")          # host tensor for a device call
+    bad_out = [torch.zeros(3, dtype=torch.float32), torch.zeros(2, dtype=torch.float64),
+               torch.zeros(6, dtype=torch.float64)[::2], torch.zeros(3, dtype=torch.float64, device="meta")]
+    for o in bad_out:
+        with pytest.raises(ValueError):
+            noalloc_args(Y, o, N, device_type="cpu")

@@ -200,6 +200,27 @@ def test_kron_levels_eps_and_parity(pkg):
         check_solution(A, y, lam, x, xs, gap, 1e-6, kept)
 
 
+def test_kron_without_normalisation(pkg):
+    """normalize = 0 keeps the Kronecker sum as given (d = 1, atoms of any norm): the stored exact
+    atoms, the truncations' eps_j and the solutions match the oracle's unscaled operator."""
+    w = S.kron_small(R=3, N1=6, K1=8, N2=5, K2=9, n_signals=3, seed=5, p=0.08)
+    d = pkg.Dictionary.kron(w.Bf, w.Cf, normalize=False).add_level(pkg.LEVEL_KRON, 1)
+    ones = np.ones(w.Bf.shape[2] * w.Cf.shape[2])
+    A = OD.KronDict(w.Bf, w.Cf, ones).dense()
+    assert np.ptp(np.linalg.norm(A, axis=0)) > 0.1          # the atoms are not unit-norm
+    e0, _ = d.level_data(0, atoms=False)
+    np.testing.assert_allclose(e0, OD.kron_truncation_eps_gram(w.Bf, w.Cf, ones, 1), rtol=1e-9, atol=1e-14)
+    e1, a1 = d.level_data(1)
+    np.testing.assert_allclose(a1, OD.to_f32(A).T, rtol=0, atol=0)
+    for b in range(3):
+        y = w.Y[b]
+        lam = w.lam_ratio[b] * OL.lambda_max(A.T @ y)
+        xs = exact_solution(A, y, lam)
+        x, gap, kept, st = d.solve(y, lam, 1e-6)
+        check_solution(A, y, lam, x, xs, gap, 1e-6, kept)
+    d.close()
+
+
 @pytest.mark.parametrize("ratio", [0.3, 0.5, 0.8])
 def test_c2_structured(pkg, ratio):
     """c2 at full size: R = 4 terms of 32 x 64, truncations R = 1, 2, then the exact atoms."""

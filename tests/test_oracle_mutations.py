@@ -34,12 +34,22 @@ def _radius_without_delta(Gp, delta, lam):
     return float(np.sqrt(max(2.0 * Gp, 0.0))) / lam
 
 
+def _projection_without_lam(y, z, lam):
+    return float(y @ z) / float(z @ z)
+
+
+def _stable_lambda_max_without_eps(Atty, eps, ynorm):
+    return float(np.max(np.abs(Atty)))
+
+
 CASES = [
     ("soft_threshold", _wrong_threshold, lambda: P.test_brute_force_sign_enumeration(0, 0.5)),
     ("dual_of_multiple", _dual_sign_slip, lambda: P.test_brute_force_sign_enumeration(1, 0.5)),
     ("stable_sphere_test", _stable_test_without_eps, lambda: P.test_stable_zone_test_bounds_every_atom_in_the_zone()),
     ("theta_dynamic_coef", _coef_without_clip, lambda: P.test_gap_safe_sphere_exact_dictionary()),
     ("stable_gap_radius", _radius_without_delta, lambda: P.test_theorem1_stable_gap_sphere_contains_theta_star(0)),
+    ("projection_coefficient", _projection_without_lam, lambda: P.test_projection_coefficient_is_the_orthogonal_projection()),
+    ("stable_lambda_max", _stable_lambda_max_without_eps, lambda: P.test_stable_lambda_max_bounds_lambda_max()),
 ]
 
 

@@ -114,6 +114,50 @@ def test_proposition1_optimal_scaling_by_grid_search():
         assert np.max(np.abs(A.T @ (s * z))) <= 1 + 1e-12
 
 
+def test_projection_coefficient_is_the_orthogonal_projection():
+    """Prop. 1's beta: beta z is the orthogonal projection of y / lam on span(z), i.e. the
+    least-squares coefficient of z for y / lam (numpy's lstsq), and the remainder is orthogonal to z."""
+    r = _rng(21)
+    for _ in range(20):
+        N = int(r.integers(3, 40))
+        y, z = r.standard_normal(N), r.standard_normal(N)
+        lam = float(r.uniform(0.05, 3.0))
+        beta = L.projection_coefficient(y, z, lam)
+        ls = np.linalg.lstsq(z[:, None], y / lam, rcond=None)[0][0]
+        assert abs(beta - ls) <= 1e-12 * max(abs(ls), 1e-300)
+        assert abs(float(z @ (y / lam - beta * z))) <= 1e-12 * np.linalg.norm(z) * np.linalg.norm(y / lam)
+    # a multiple of z projects onto itself
+    z = r.standard_normal(7)
+    assert abs(L.projection_coefficient(2.5 * 0.7 * z, z, 0.7) - 2.5) <= 1e-14
+
+
+def test_stable_lambda_max_bounds_lambda_max():
+    """eq:DefStableLMax: lambda'_max = max_j |a~_j^T y| + eps_j ||y|| >= lambda_max for every
+    approximation with ||a~_j - a_j|| <= eps_j (Cauchy-Schwarz), with equality when eps = 0 and
+    A~ = A, and it is attained when each approximation error points along -sign(a_j^T y) y.
+    The Static Safe sphere built on it still contains theta* (y / lambda'_max is dual feasible)."""
+    r = _rng(22)
+    A, y, lam = _small_problem(25, 60, 7, 0.5)
+    lm = L.lambda_max(A.T @ y)
+    yn = float(np.linalg.norm(y))
+    assert L.stable_lambda_max(A.T @ y, np.zeros(60), yn) == lm
+    for _ in range(10):
+        E = r.standard_normal(A.shape)
+        eps = r.uniform(0.0, 0.2, 60)
+        E *= eps / np.linalg.norm(E, axis=0)
+        At = A + E
+        assert L.stable_lambda_max(At.T @ y, eps, yn) >= lm * (1 - 1e-12)
+    # tight case: a~_j = a_j - eps_j sign(a_j^T y) y / ||y|| with eps_j < |a_j^T y| / ||y||
+    c = A.T @ y
+    eps = 0.5 * np.abs(c) / yn
+    At = A - (eps * np.sign(c))[None, :] * (y / yn)[:, None]
+    np.testing.assert_allclose(np.abs(At.T @ y), np.abs(c) - eps * yn, rtol=1e-12)
+    assert abs(L.stable_lambda_max(At.T @ y, eps, yn) - lm) <= 1e-12 * lm
+    xs, ts = _theta_star(A, y, lam)
+    cen, R = L.static_sphere(y, lam, L.stable_lambda_max(At.T @ y + 0.0, 2 * eps, yn))
+    assert np.linalg.norm(ts - cen) <= R * (1 + 1e-12)
+
+
 # ----------------------------------------------------------------------------- sphere tests
 
 def test_sphere_test_closed_form_and_maximiser():

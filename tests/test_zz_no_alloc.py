@@ -41,6 +41,46 @@ def test_noalloc_lambda_max_matches_regular_entry_point(pkg, dtype, N, K, B):
     d.close()
 
 
+def test_noalloc_alone_on_a_fresh_dictionary_allocates_nothing(pkg):
+    """First call on a new dictionary, with no regular call before it: the result matches an
+    FP64 host evaluation of ||A^T y||_inf, and free device memory is the same before and after
+    two calls.  A warm-up call on another dictionary first loads the library's kernels, whose
+    module (with the fixed scratch array) is mapped once per process."""
+    w0 = S.dense_small(N=64, K=256, n_signals=2, seed=5)
+    d0 = pkg.Dictionary.dense(w0.A, dtype="f32")
+    d0.lambda_max_noalloc(torch.tensor(w0.Y, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    d0.close()
+    w = S.dense_small(N=1000, K=3000, n_signals=9, seed=17)
+    d = pkg.Dictionary.dense(w.A, dtype="f32")
+    Y = torch.tensor(w.Y, dtype=torch.float32, device="cuda")
+    out = torch.full((9,), -1.0, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        d.lambda_max_noalloc(Y, out)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        np.testing.assert_allclose(out.cpu().numpy(), np.max(np.abs(w.Y @ w.A), axis=1), rtol=1e-6)
+    d.close()
+
+
+def test_noalloc_rejects_bad_buffers_before_the_call(pkg):
+    """Buffers the kernel could overrun are refused by the binding (ValueError)."""
+    w = S.dense_small(N=64, K=256, n_signals=4, seed=3)
+    d = pkg.Dictionary.dense(w.A, dtype="f32")
+    Y = torch.tensor(w.Y, dtype=torch.float32, device="cuda")
+    for bad in (torch.zeros(4, dtype=torch.float32, device="cuda"), torch.zeros(3, dtype=torch.float64, device="cuda"),
+                torch.zeros(4, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            d.lambda_max_noalloc(Y, bad)
+    with pytest.raises(ValueError):
+        d.lambda_max_noalloc(Y.double())
+    with pytest.raises(ValueError):
+        d.lambda_max_noalloc(Y[:, :32].contiguous())
+    d.close()
+
+
 def test_noalloc_rejects_oversized_batches(pkg):
     """B * ceil(K / 256) above the fixed scratch size is refused before any work is queued."""
     w = S.dense_small(N=64, K=8192, n_signals=1, seed=1)
