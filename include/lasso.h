@@ -148,7 +148,10 @@ typedef struct {
     int final_fp64;          /* 1: append an FP64-accumulation rung on the exact data and keep
                                 FP64 iterates (tight tolerances; default 0).  The gaps certify
                                 the FP64 iterates: lasso_solve returns them as they are, the
-                                batch calls return their rounding to FP32                      */
+                                batch calls return their rounding to FP32.  Set automatically
+                                for FP32 dictionaries when tol < 1e-7: an FP32 point cannot be
+                                certified much below that (its dual point's gap is first order
+                                in the point's rounding)                                      */
     int certify_full;        /* 1: audit with an explicit full-dictionary pass at exit (default
                                 0): every atom recomputed with error-free products            */
     int passes_per_sync;     /* passes per captured CUDA graph replay (default 8)               */
@@ -168,6 +171,16 @@ typedef struct {
                                 the deciding atoms from the FP32 data.  Default 0: the tensor
                                 cores' FP32 accumulation is too coarse for the last decades of
                                 the gap (FISTA needs more passes, some signals stall near 1e-6) */
+    int split_level;         /* 1 (default): with tensor_cores, a batch of at least 256 signals and an
+                                FP32 dense exact level, one more approximate level runs just
+                                before the exact one: the split BF16 pair a1 + a2 of the exact
+                                atoms (a - a1 - a2 = e3, |e3| <= 2^-16 |a|), correlated on the
+                                tensor cores as a1^T r1 + a1^T r2 + a2^T r1 with promoted
+                                accumulation; its residual is the exact one, and the
+                                correlation error (||e3_j||, the dropped terms, the rounding)
+                                enters the stable test as an approximation error (Section III).
+                                It takes the solve's middle decades off the exact level.  RC
+                                0.02 (Algorithm 2).  Ignored with tc_exact.  0: no split level */
     int fp64_fallback;       /* 1 (default): a signal whose certificate stops improving on the exact
                                 FP32 level (FP32 iterates at their precision floor, e.g. on very
                                 coherent dictionaries) is stopped and solved again from scratch

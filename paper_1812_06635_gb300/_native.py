@@ -29,6 +29,7 @@ class LassoOpts(C.Structure):
         ("profile", C.c_int),
         ("full_gap", C.c_int),
         ("tc_exact", C.c_int),
+        ("split_level", C.c_int),
         ("fp64_fallback", C.c_int),
         ("autotune", C.c_int),
         ("kept_mask", C.c_void_p),

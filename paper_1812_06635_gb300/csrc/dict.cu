@@ -569,12 +569,12 @@ static void level_rounding(const lasso_dict* d, const HostLevel& h, bool vt_doub
     return;
   }
   if (tc && h.kind == LK_F32) {
-    // split exact level on the tensor cores: 3 (N + N / 16) BF16 products accumulated (the
-    // three partial products summed in one accumulator), then the FP32 store; the sum of
-    // |a1 r1| + |a1 r2| + |a2 r1| is <= (1 + 2^-7)^2 kappa_j ||rho||.  The certificate atoms are
-    // recomputed from the FP32 data with error-free products (gam_tight), the residual as for
-    // the FP32 level.
-    L.gam_corr = 1.02 * gamma_n(3.0 * (N + N / 16.0) + 3.0, TC_U_BF16) + stage;
+    // split form on the tensor cores: the three BF16 products a1 r1, a1 r2, a2 r1 with promoted
+    // accumulation (each k-block a tensor-core chain, the k-block sums added in FP32), then the
+    // FP32 store; the sum of |a1 r1| + |a1 r2| + |a2 r1| is <= (1 + 2^-7)^2 kappa_j ||rho||.  The
+    // certificate atoms are recomputed from the FP32 data with error-free products (gam_tight),
+    // the residual as for the FP32 level.
+    L.gam_corr = 1.02 * tc_promoted_gamma(d->ldN, 3) + 2.0 * U32 + stage;
     L.gam_tight = 2.0 * gamma_n(2.0 * nl, U32) * gamma_n(2.0 * nl, U32) + stage;
     L.res_model = RES_DOT2;
     L.gam_res = vt_double ? U32 : 0.0;
@@ -769,7 +769,7 @@ int ensure_rung64(lasso_dict* d) {
 static bool dict_trace() { return getenv("LASSO_TRACE_STEPS") != nullptr; }
 
 int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order,
-                   bool tc_levels, bool tc_exact) {
+                   bool tc_levels, bool tc_exact, bool split_level) {
   if (dict_trace()) fprintf(stderr, "[lasso trace] build_dict_dev: enter\n");
   memset(out, 0, sizeof(*out));
   out->N = (int)d->N;
@@ -794,6 +794,13 @@ int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<con
   if (dict_trace()) fprintf(stderr, "[lasso trace] build_dict_dev: atom norms ready\n");
   std::vector<const HostLevel*> lv;
   for (auto& h : d->approx) lv.push_back(&h);
+  const bool vt64 = final_fp64 || d->exact_kind == LK_F64;
+  split_level = split_level && !tc_exact && !vt64 && d->exact_kind == LK_F32 && d->exact.data;
+  if (split_level) {
+    int rc = ensure_split(d);
+    if (rc) return rc;
+    lv.push_back(&d->exact);   // the split form of the exact atoms (tensor cores)
+  }
   lv.push_back(&d->exact);
   if (final_fp64 && d->exact_kind == LK_F32) {
     int rc = ensure_rung64(d);
@@ -807,9 +814,13 @@ int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<con
     int rc = ensure_split(d);
     if (rc) return rc;
   }
+  const size_t split_idx = split_level ? d->approx.size() : lv.size();   // first entry of the exact atoms
   for (size_t i = 0; i < lv.size(); ++i) {
     const bool is_exact = lv[i] == &d->exact;
-    out->lv[i] = make_level_dev(d, *lv[i], vt_double, is_exact ? (tc_exact && !vt_double) : tc_levels);
+    const bool is_split = i == split_idx;
+    out->lv[i] = make_level_dev(d, *lv[i], vt_double,
+                                is_split ? true : (is_exact ? (tc_exact && !vt_double) : tc_levels));
+    if (is_split) out->lv[i].rc = SPLIT_RC;
     if (!out->lv[i].epsr32) return LASSO_ERR_CUDA;
   }
   if (order) *order = lv;

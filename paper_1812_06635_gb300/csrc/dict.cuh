@@ -76,8 +76,11 @@ LevelDev make_level_dev(const lasso_dict* d, const HostLevel& h, bool vt_double 
 // All levels of a solve, coarsest first, exact (or the FP64 rung) last.  tc_levels: run the
 // batched BF16 / FP8 correlations on the tensor cores; tc_exact: the exact FP32 level too, in
 // its split BF16 form.
+// split_level: one more level before the exact one, the split BF16 pair of the exact FP32 atoms
+// correlated on the tensor cores (relative complexity SPLIT_RC).
 int build_dict_dev(lasso_dict* d, bool final_fp64, DictDev* out, std::vector<const HostLevel*>* order,
-                   bool tc_levels = false, bool tc_exact = false);
+                   bool tc_levels = false, bool tc_exact = false, bool split_level = false);
+constexpr double SPLIT_RC = 0.02;
 // BF16 split of the exact FP32 level and its bounds (computed once).
 int ensure_split(lasso_dict* d);
 int ensure_rung64(lasso_dict* d);

@@ -24,6 +24,7 @@ constexpr int FULL_SET = MAX_LEVELS - 1;    // slot list of the signals under th
 constexpr int CORR_THREADS = 256;
 constexpr int RES_ROWS = RES_THREADS * 4;   // rows per residual block
 constexpr int GEMM_T = 64;                  // tile of the Kronecker small GEMMs
+constexpr double FP32_TOL_FLOOR = 1e-7;     // smallest tolerance solved with FP32 iterates
 
 struct Workspace {
   int64_t B = 0, K = 0, ldN = 0;
@@ -2363,7 +2364,9 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   for (auto& h : d->approx) any_approx |= h.kind == LK_BF16 || h.kind == LK_FP8;
   const bool want_tc = tc_batch && any_approx;
   const bool tc_exact = tc_batch && o.tc_exact && sizeof(VT) == 4 && !o.final_fp64 && d->exact_kind == LK_F32;
-  int rc = build_dict_dev(d, o.final_fp64 != 0, &pa.dd, &order, want_tc, tc_exact);
+  const bool split_lv = tc_batch && o.split_level && !tc_exact && sizeof(VT) == 4 && !o.final_fp64 &&
+                        d->exact_kind == LK_F32;
+  int rc = build_dict_dev(d, o.final_fp64 != 0, &pa.dd, &order, want_tc, tc_exact, split_lv);
   if (rc) return rc;
   std::vector<TcJob> tc_jobs;
   for (int l = 0; l < pa.dd.n_levels; ++l) {
@@ -2471,8 +2474,12 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   k_init_finish<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa, o.lambda_relative);
   pa.sp.corr_grid = corr_grid;
   // the full-dictionary check uses the same tensor-core level when the exact level is FP32 data
-  const TcJob* full_job =
-      sizeof(VT) == 4 && pa.dd.lv[pa.dd.n_levels - 1].kind == LK_F32 && pa.sp.full_gap ? init_job : nullptr;
+  // and that level is BF16: the E4M3 level's bounds (eps_j of a few percent) let most rejected
+  // atoms reach the preserved maximum, and each of those is recomputed from its exact row
+  const TcJob* full_job = sizeof(VT) == 4 && pa.dd.lv[pa.dd.n_levels - 1].kind == LK_F32 && pa.sp.full_gap &&
+                                  init_job && !init_job->fp8
+                              ? init_job
+                              : nullptr;
   k_schedule<VT><<<1, 1024, 0, st>>>(pa, 1);
   LASSO_CUDA_TRY(cudaGetLastError());
   LASSO_CUDA_TRY(cudaMemsetAsync(w->alg_bytes, 0, 16 * sizeof(double), st));
@@ -2635,6 +2642,7 @@ extern "C" void lasso_opts_default(lasso_opts* o) {
   o->profile = 0;
   o->full_gap = 1;
   o->tc_exact = 0;
+  o->split_level = 1;
   o->fp64_fallback = 1;
   o->autotune = 1;
 }
@@ -2777,6 +2785,10 @@ static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
     int rc = dict_prepare(d, 0.0);
     if (rc) return rc;
   }
+  // FP32 iterates cannot carry a certificate much below 1e-7: the duality gap of the dynamic dual
+  // point is first order in the point's rounding (about 6e-8 relative).  Tighter tolerances on
+  // an FP32 dictionary run the FP64-accumulation rung with FP64 iterates (as final_fp64 does).
+  if (d->exact_kind == LK_F32 && io.tol < FP32_TOL_FLOOR && !io.point_f32) io.opts.final_fp64 = 1;
   const bool vt_double = d->exact_kind == LK_F64 || io.opts.final_fp64;
   Workspace* w = nullptr;
   int rc = get_ws(d, io.B, vt_double, &w);

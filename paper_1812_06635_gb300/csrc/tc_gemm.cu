@@ -232,6 +232,171 @@ k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUten
   if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The same product with promoted accumulation.  The MMAs of k-block g (TC_GROUP consecutive
+// 128-byte K-slices, over the phases in order) accumulate from zero into TMEM buffer g % 2
+// (columns [256 (g % 2), 256 (g % 2) + 256)); when a k-block's MMAs complete, the eight epilogue
+// warps load it with tcgen05.ld and add it to FP32 registers (round to nearest), then release the
+// buffer.  Warp 2 + e reads TMEM lane quarter (warp % 4) and the column half e / 4, so each
+// epilogue thread holds 128 running sums (one atom, 128 signals).  The tensor-core accumulation
+// chain is one k-block long; the k-block sums are added in FP32.
+template <int FP8>
+__global__ void __launch_bounds__(TCP_THREADS, 1)
+k_tc_corr_kb(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb,
+             const __grid_constant__ CUtensorMap tma2, const __grid_constant__ CUtensorMap tmb2, int64_t K, int64_t B,
+             int nkb, int nphase, const float* __restrict__ scale, const float* __restrict__ sigma,
+             const int* __restrict__ list, const int* __restrict__ count, float* __restrict__ Gfull,
+             int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t tc_smem[];
+  __shared__ int s_fail;
+  __shared__ uint8_t s_on[TC_BN];
+  __shared__ float s_sigma[TC_BN];
+  __shared__ int s_sig[TC_BN];
+  __shared__ uint32_t s_tmem;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = base;
+  uint8_t* sB = base + TC_STAGES * TC_BM * 128;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_BN * 128);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* accf = empty + TC_STAGES;     // [2]: k-block in buffer b complete (tcgen05.commit)
+  uint64_t* acce = accf + 2;              // [2]: buffer b read by the 8 epilogue warps
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
+  const int64_t n0 = (int64_t)blockIdx.y * TC_BN;
+  const int64_t nslots = count ? (int64_t)*count : B;
+  if (n0 >= nslots) return;
+  if (threadIdx.x == 0) s_fail = 0;
+  for (int i = threadIdx.x; i < TC_BN; i += TCP_THREADS) {
+    const int64_t slot = n0 + i;
+    const bool on = slot < nslots;
+    const int b = on ? (list ? list[slot] : (int)slot) : 0;
+    s_on[i] = on ? 1 : 0;
+    s_sig[i] = b;
+    s_sigma[i] = on ? (sigma ? sigma[b] : 1.f) : 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accf[0], 1);
+    mbar_init(&accf[1], 1);
+    mbar_init(&acce[0], 8);
+    mbar_init(&acce[1], 8);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(2 * TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  constexpr int KB_ELEMS = FP8 ? 128 : 64;
+  const int nk = nkb * nphase;
+  const int ng = (nk + TC_GROUP - 1) / TC_GROUP;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+        const int phase = kb / nkb, kk = kb - phase * nkb;
+        if (kb >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+          s_fail = 1;
+          break;
+        }
+        mbar_expect_tx(&full[s], (uint32_t)(TC_BM + TC_BN) * 128u);
+        tma_load_2d(phase == 2 ? &tma2 : &tma, &full[s], sA + s * TC_BM * 128, kk * KB_ELEMS, (int)m0);
+        tma_load_2d(phase == 1 ? &tmb2 : &tmb, &full[s], sB + s * TC_BN * 128, kk * KB_ELEMS, (int)n0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc(FP8 ? 0u : 1u, TC_BM, TC_BN);
+      for (int kb = 0; kb < nk; ++kb) {
+        const int g = kb / TC_GROUP;
+        const bool first = (kb % TC_GROUP) == 0;
+        const int buf = g & 1;
+        if (first && g >= 2) {
+          // the epilogue has read this buffer's previous k-block
+          if (!mbar_wait(&acce[buf], (uint32_t)((g >> 1) - 1) & 1u)) {
+            s_fail = 1;
+            break;
+          }
+          tc_fence_after();
+        }
+        const int s = kb % TC_STAGES;
+        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+        if (!mbar_wait(&full[s], ph)) {
+          s_fail = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t ad = umma_sdesc(smem_u32(sA + s * TC_BM * 128));
+        const uint64_t bd = umma_sdesc(smem_u32(sB + s * TC_BN * 128));
+        const uint32_t dst = tmem + (uint32_t)(buf * TC_BN);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) umma<FP8>(dst, ad + 2 * k, bd + 2 * k, idesc, (first && k == 0) ? 0u : 1u);
+        umma_commit(&empty[s]);
+        if ((kb % TC_GROUP) == TC_GROUP - 1 || kb == nk - 1) umma_commit(&accf[buf]);
+      }
+    }
+  } else {
+    const int e = warp - 2;
+    const int q = warp & 3;                  // TMEM lane quarter this warp may read
+    const int h = e >> 2;                    // column half
+    const int64_t row = m0 + q * 32 + lane;
+    float acc[TC_BN / 2];
+#pragma unroll
+    for (int i = 0; i < TC_BN / 2; ++i) acc[i] = 0.f;
+    bool ok = true;
+    for (int g = 0; g < ng; ++g) {
+      const int buf = g & 1;
+      if (!mbar_wait(&accf[buf], (uint32_t)(g >> 1) & 1u)) {
+        ok = false;
+        s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < TC_BN / 64; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN + h * (TC_BN / 2) + c * 32), r);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[c * 32 + i] = __fadd_rn(acc[c * 32 + i], __uint_as_float(r[i]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
+    }
+    const float sc = row < K ? (scale ? scale[row] : 1.f) : 0.f;
+    if (ok && row < K) {
+#pragma unroll
+      for (int i = 0; i < TC_BN / 2; ++i) {
+        const int col = h * (TC_BN / 2) + i;
+        if (s_on[col]) Gfull[(int64_t)s_sig[col] * K + row] = acc[i] * sc * s_sigma[col];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
+  }
+  if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+}
+
 // ------------------------------------------------------------------ host side
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -276,6 +441,7 @@ int tc_make_operands(const void* level_data, const void* level_data2, int64_t K,
     return LASSO_ERR_INVALID_ARG;
   out->fp8 = fp8;
   out->nphase = split ? 3 : 1;
+  out->promote = split ? 1 : 0;
   int rc = encode_2d(&out->a, level_data, K, ldN, fp8, TC_BM);
   if (rc) return rc;
   rc = encode_2d(&out->b, rq, B, ldN, fp8, TC_BN);
@@ -294,9 +460,19 @@ void tc_launch_corr(const TcOperands& ops, int64_t K, int64_t B, int64_t ldN, co
                     const float* sigma, const int* list, const int* count, float* Gfull, int* err,
                     cudaStream_t stream) {
   static bool attr[2] = {false, false};
+  static bool attr_kb = false;
   const int es = ops.fp8 ? 1 : 2;
   const int nkb = (int)((ldN * es + 127) / 128);   // 128-byte K-slices (TMA zero-fills the tail)
   const dim3 grid((unsigned)((K + TC_BM - 1) / TC_BM), (unsigned)((B + TC_BN - 1) / TC_BN));
+  if (ops.promote && !ops.fp8) {
+    if (!attr_kb) {
+      cudaFuncSetAttribute(k_tc_corr_kb<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCP_SMEM);
+      attr_kb = true;
+    }
+    k_tc_corr_kb<0><<<grid, TCP_THREADS, TCP_SMEM, stream>>>(ops.a, ops.b, ops.a2, ops.b2, K, B, nkb, ops.nphase,
+                                                             scale, sigma, list, count, Gfull, err);
+    return;
+  }
   if (ops.fp8) {
     if (!attr[1]) {
       cudaFuncSetAttribute(k_tc_corr<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
@@ -411,7 +587,10 @@ int tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel, doub
     if (rc) break;
     tc_launch_corr(ops, K, B, ld, nullptr, nullptr, nullptr, nullptr, G, err, 0);
     const int nk = (int)(ld / (fp8 ? 32 : 16));
-    const double gam = gamma_n(((double)ld + nk) * (split ? 3.0 : 1.0), fp8 ? TC_U_FP8 : TC_U_BF16);
+    // split (promoted): one k-block's chain of TC_GROUP * 64 products and 4 TC_GROUP k-steps with
+    // u_tc, then the FP32 sum of the k-blocks; plain: one chain over all products
+    const double gam = split ? tc_promoted_gamma(ld, 3)
+                             : gamma_n(((double)ld + nk), fp8 ? TC_U_FP8 : TC_U_BF16);
     k_tc_check<<<(unsigned)((K * B + 255) / 256), 256>>>(A, R, A2, R2, G, K, B, ld, fp8, gam, out);
     int herr = 0;
     unsigned long long h[2] = {0, 0};

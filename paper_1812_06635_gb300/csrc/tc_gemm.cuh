@@ -20,13 +20,37 @@ constexpr int TC_SMEM = TC_STAGES * (TC_BM + TC_BN) * 128 + 1024 + 256;
 constexpr double TC_U_BF16 = 2.384185791015625e-07;   // 2^-22
 constexpr double TC_U_FP8 = 1.9073486328125e-06;      // 2^-19
 
+// Promoted accumulation (the split form): the MMAs of each k-block of TC_GROUP 128-byte
+// K-slices accumulate in one of two TMEM buffers; eight epilogue warps add every finished
+// k-block into FP32 registers (round to nearest) while the next k-block accumulates in the other
+// buffer.  The tensor-core chain then spans one k-block instead of the whole signal length.
+constexpr int TC_GROUP = 2;                 // 128-byte K-slices per promoted k-block
+constexpr int TCP_THREADS = 320;            // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int TCP_SMEM = TC_SMEM;
+
 struct TcOperands {
   CUtensorMap a;          // dictionary level: K rows (atoms) x ldN, K-major
   CUtensorMap b;          // quantised residuals: B rows (signal slots) x ldN, K-major
   CUtensorMap a2, b2;     // split form (nphase 3): second BF16 parts of the atoms / residuals
   int fp8;                // 1: kind::f8f6f4 E4M3, 0: kind::f16 BF16
   int nphase;             // 1: a^T r; 3: a1^T r1 + a1^T r2 + a2^T r1 in one accumulator
+  int promote;            // 1: promoted accumulation (k-blocks of TC_GROUP slices summed in FP32)
 };
+
+// Number of promoted k-blocks of a product of ldN elements in `nphase` phases.
+inline int tc_groups(int64_t ldN, int fp8, int nphase) {
+  const int nkb = (int)((ldN * (fp8 ? 1 : 2) + 127) / 128);
+  return (nkb * nphase + TC_GROUP - 1) / TC_GROUP;
+}
+
+// Rounding bound of the promoted BF16 product relative to sum |a_i r_i| (all phases): each
+// k-block is a tensor-core chain of TC_GROUP (64 products + 4 k-steps) with unit roundoff
+// u_tc = 2^-22, and the k-block sums are added in FP32 with round to nearest.
+inline double tc_promoted_gamma(int64_t ldN, int nphase) {
+  const double gk = gamma_n(TC_GROUP * (64.0 + 4.0), TC_U_BF16);
+  const double gr = gamma_n((double)tc_groups(ldN, 0, nphase), U32);
+  return gk + gr * (1.0 + gk);
+}
 
 // Encode the tensor maps (host); level_data2 / rq2 non-null selects the split form.  Returns
 // LASSO_OK or an error status.
@@ -43,7 +67,7 @@ void tc_launch_corr(const TcOperands& ops, int64_t K, int64_t B, int64_t ldN, co
 
 // Self-test: random K x N operands and B signals through the tensor-core GEMM, compared with an
 // FP64 evaluation of the same products; reports the largest error relative to sum |a_i r_i|.
-// mode 0: BF16, 1: E4M3, 2: split BF16 (three products in one accumulator).
+// mode 0: BF16, 1: E4M3, 2: split BF16 (three products, promoted accumulation).
 int tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel, double* max_abs_bound_ratio);
 
 }  // namespace lasso

@@ -96,15 +96,18 @@ def test_faust_ladder_batch_parity(pkg, N, K):
     d = _dict(pkg, w)
     Y = torch.tensor(w.Y, dtype=torch.float32, device="cuda")
     lam = np.array([w.lam_ratio[b] * OL.lambda_max(w.A.T @ w.Y[b]) for b in range(6)])
-    X, gaps, status, iters, st = d.solve_batch(Y, torch.tensor(lam, device="cuda"), tol=1e-6, certify_full=1)
+    kept = torch.zeros((6, w.K), dtype=torch.uint8, device="cuda")
+    X, gaps, status, iters, st = d.solve_batch(Y, torch.tensor(lam, device="cuda"), tol=1e-6, certify_full=1,
+                                               kept=kept)
     assert np.all(status.cpu().numpy() == 0)
     assert st.level_passes[0] >= 6                     # the first pass of every signal is on level 0
     X = X.double().cpu().numpy()
     gaps = gaps.cpu().numpy()
+    kept = kept.cpu().numpy()
     refs = [exact_solution(w.A, w.Y[b], lam[b]) for b in range(6)]
     for b in range(6):
         assert gaps[b] <= 1e-6
-        check_solution(w.A, w.Y[b], lam[b], X[b], refs[b], gaps[b], 1e-6)
+        check_solution(w.A, w.Y[b], lam[b], X[b], refs[b], gaps[b], 1e-6, kept=np.flatnonzero(kept[b]))
     X2, gaps2, status2, _, _ = d.solve_batch(Y, torch.tensor(lam, device="cuda"), tol=1e-11, final_fp64=1,
                                              max_iter=100000)
     assert np.all(status2.cpu().numpy() == 0)
@@ -146,15 +149,18 @@ def test_meg_faust_full_size(pkg):
     for b in ref["signals"]:
         assert abs(float(lmax[b]) - float(ref[f"s{b}_lmax"])) <= 1e-6 * float(ref[f"s{b}_lmax"])
         lam[b] = float(ref[f"s{b}_lam"])
-    X, gaps, status, iters, st = d.solve_batch(Y, lam, tol=tol)
+    kept = torch.zeros((50, w.K), dtype=torch.uint8, device="cuda")
+    X, gaps, status, iters, st = d.solve_batch(Y, lam, tol=tol, kept=kept)
     assert bool((status == 0).all())
     assert float(gaps.max()) <= tol
     assert st.level_passes[0] >= 50
     Xh = X.double().cpu().numpy()
+    kh = kept.cpu().numpy().astype(bool)
     for b in ref["signals"]:
         y, la = w.Y[b], float(ref[f"s{b}_lam"])
         xs = np.zeros(w.K)
         xs[ref[f"s{b}_idx"]] = ref[f"s{b}_val"]
+        assert kh[b][np.flatnonzero(xs)].all(), b      # no atom of the minimiser was rejected
         yy = float(y @ y)
 
         def P(x):

@@ -241,9 +241,16 @@ def test_c2_structured(pkg, ratio):
 def test_c3_full_batch_sampled(pkg):
     """Full c3 batch (4096 signals, 2048 x 8192) in the bench's launch configuration.
 
-    Every signal is checked by its status and certificate; four signals are compared with the
-    oracle minimisers stored in tests/golden/c3_reference.npz (written by make_references.py):
-    the full-dictionary FP64 gap of the GPU point is <= tol and ||A (x - x*)||^2 <= 2 G ||y||^2.
+    Every signal is checked by its status and certificate; 20 signals (the lambda / lambda_max and
+    density extremes, the ragged end of the batch) are compared with the oracle minimisers stored
+    in tests/golden/c3_reference.npz (written by make_references.py, which calls only oracle/):
+    * tol 1e-6: the oracle's full-dictionary FP64 gap of the GPU point is <= tol and <= the GPU
+      certificate, ||A (x - x*)||^2 <= 2 G ||y||^2, and the batch's preserved set (kept_mask)
+      contains the support of x* (no unsafe rejection);
+    * tol 1e-12 (FP64 rung): ||x - x*|| <= 1e-5 ||x*|| element by element, with the same safety.
+    A relative gap of 1e-6 bounds ||A (x - x*)|| by sqrt(2e-6) ||y|| only: signals whose minimiser
+    has a few tiny entries (lambda near lambda_max) sit far above 1e-5 in relative x error at that
+    tolerance, which is why the element-wise bar is asserted at the tighter one.
     """
     import os
     ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "c3_reference.npz"))
@@ -253,17 +260,34 @@ def test_c3_full_batch_sampled(pkg):
     Y = torch.tensor(w.Y, dtype=torch.float32, device="cuda")
     lmax = d.lambda_max(Y)
     lam = torch.tensor(w.lam_ratio, dtype=torch.float64, device="cuda") * lmax
-    for b in ref["signals"]:
+    sig = [int(b) for b in ref["signals"]]
+    assert len(sig) >= 16 and 4095 in sig
+    for b in sig:
         assert abs(float(lmax[b]) - float(ref[f"s{b}_lmax"])) <= 1e-6 * float(ref[f"s{b}_lmax"])
         lam[b] = float(ref[f"s{b}_lam"])
-    X, gaps, status, iters, st = d.solve_batch(Y, lam, tol=1e-6, certify_full=1)
-    assert bool((status == 0).all())
-    assert float(gaps.max()) <= 1e-6
-    Xh = X.double().cpu().numpy()
-    for b in ref["signals"]:
+    xs_all = {}
+    for b in sig:
         xs = np.zeros(A.shape[1])
         xs[ref[f"s{b}_idx"]] = ref[f"s{b}_val"]
-        check_solution(A, w.Y[b], float(ref[f"s{b}_lam"]), Xh[b], xs, float(gaps[b]), 1e-6)
+        xs_all[b] = xs
+    for tol, kw in ((1e-6, {"certify_full": 1}), (1e-12, {"final_fp64": 1})):
+        kept = torch.zeros((4096, A.shape[1]), dtype=torch.uint8, device="cuda")
+        X, gaps, status, iters, st = d.solve_batch(Y, lam, tol=tol, kept=kept, **kw)
+        assert bool((status == 0).all())
+        assert float(gaps.max()) <= tol
+        Xh = X.double().cpu().numpy()
+        kh = kept.cpu().numpy().astype(bool)
+        assert not np.any((Xh != 0) & ~kh)             # x is zero outside the preserved set
+        errs = []
+        for b in sig:
+            xs = xs_all[b]
+            assert kh[b][np.flatnonzero(xs)].all(), (tol, b)  # safety: supp(x*) is preserved
+            if tol >= 1e-6:
+                check_solution(A, w.Y[b], float(ref[f"s{b}_lam"]), Xh[b], xs, float(gaps[b]), tol)
+            errs.append(np.linalg.norm(Xh[b] - xs) / np.linalg.norm(xs))
+        print(f"c3 tol {tol:g}: relative x error median {np.median(errs):.2e} max {np.max(errs):.2e}")
+        if tol <= 1e-12:
+            assert max(errs) <= 1e-5, errs
     d.close()
 
 
