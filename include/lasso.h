@@ -149,7 +149,7 @@ typedef struct {
                                 FP64 iterates (tight tolerances; default 0).  The gaps certify
                                 the FP64 iterates: lasso_solve returns them as they are, the
                                 batch calls return their rounding to FP32.  Set automatically
-                                for FP32 dictionaries when tol < 1e-7: an FP32 point cannot be
+                                for FP32 dictionaries when tol < 5e-7: an FP32 point cannot be
                                 certified much below that (its dual point's gap is first order
                                 in the point's rounding)                                      */
     int certify_full;        /* 1: audit with an explicit full-dictionary pass at exit (default

@@ -24,7 +24,8 @@ constexpr int FULL_SET = MAX_LEVELS - 1;    // slot list of the signals under th
 constexpr int CORR_THREADS = 256;
 constexpr int RES_ROWS = RES_THREADS * 4;   // rows per residual block
 constexpr int GEMM_T = 64;                  // tile of the Kronecker small GEMMs
-constexpr double FP32_TOL_FLOOR = 1e-7;     // smallest tolerance solved with FP32 iterates
+constexpr int FULL_ITEM_MULT = 8;           // correlation items of levels gathered from a batched product
+constexpr double FP32_TOL_FLOOR = 5e-7;     // smallest tolerance solved with FP32 iterates
 
 struct Workspace {
   int64_t B = 0, K = 0, ldN = 0;
@@ -49,7 +50,9 @@ struct Workspace {
   double* part_res = nullptr;        // B x nrb x 2
   double* part_corr = nullptr;       // B x nch x 2
   int32_t* offsets = nullptr;        // B + 1
-  int32_t* counters = nullptr;       // [0] done count, [8 + l] signals on tensor-core level l
+  int32_t* refine_list = nullptr;    // B: signals whose certificate k_refine tightens this pass
+  int32_t* counters = nullptr;       // [0] done count, [1] stop flag, [2] chunk, [3] refine count,
+                                     // [8 + l] signals on tensor-core level l
   double* alg_bytes = nullptr;       // [6] algorithmic bytes per kernel kind
   SigState* st = nullptr;
   // Kronecker scratch
@@ -74,7 +77,8 @@ void free_ws(Workspace* w) {
   if (!w) return;
   void* ptrs[] = {w->Yw, w->Rho, w->X, w->Z, w->G, w->Xout, w->nz_val, w->nz_idx, w->kept, w->c0ub,
                   w->mask, w->cand_idx, w->cand_val, w->offsets2, w->part_full,
-                  w->part_res, w->part_corr, w->offsets, w->counters, w->alg_bytes, w->st, w->Gfull, w->AZ, w->Xd, w->Tk,
+                  w->part_res, w->part_corr, w->offsets, w->refine_list, w->counters, w->alg_bytes, w->st, w->Gfull,
+                  w->AZ, w->Xd, w->Tk,
                   w->Fs};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < MAX_LEVELS; ++l) {
@@ -142,6 +146,7 @@ static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
   rc |= ws_alloc((void**)&w->part_res, (size_t)B * w->nrb * 2 * 8);
   rc |= ws_alloc((void**)&w->part_corr, (size_t)B * w->nch * 2 * 8);
   rc |= ws_alloc((void**)&w->offsets, (size_t)(B + 1) * 4);
+  rc |= ws_alloc((void**)&w->refine_list, (size_t)B * 4);
   rc |= ws_alloc((void**)&w->counters, 64);
   rc |= ws_alloc((void**)&w->alg_bytes, 16 * sizeof(double));   // [0,6) bytes, [8,16) atom-passes per level
   rc |= ws_alloc((void**)&w->st, (size_t)B * sizeof(SigState));
@@ -195,6 +200,7 @@ struct PassArgs {
   double* part_res;
   double* part_corr;
   int32_t* offsets;
+  int32_t* refine_list;
   int32_t* counters;
   double* alg_bytes;
   SigState* st;
@@ -247,6 +253,7 @@ static void fill_pass_args(PassArgs<VT>& pa, Workspace* w, const lasso_dict* d) 
   pa.part_res = w->part_res;
   pa.part_corr = w->part_corr;
   pa.offsets = w->offsets;
+  pa.refine_list = w->refine_list;
   pa.counters = w->counters;
   pa.alg_bytes = w->alg_bytes;
   pa.st = w->st;
@@ -341,14 +348,21 @@ __global__ void k_schedule(PassArgs<VT> a, int dyn) {
   int done_total = 0;
   __syncthreads();
   const int chunk = s_chunk;
-  if (threadIdx.x == 0) a.counters[2] = chunk;
+  if (threadIdx.x == 0) {
+    a.counters[2] = chunk;
+    a.counters[3] = 0;     // the next pass's k_eval lists the signals k_refine tightens
+  }
   for (int base = 0; base < B; base += blockDim.x) {
     int b = base + threadIdx.x;
     int items = 0, dn = 0;
     if (b < B) {
       const SigState& s = a.st[b];
       dn = s.done;
-      items = s.done ? 0 : (s.n_kept + chunk - 1) / chunk;
+      // the FP32 pass (k_corr_pass) gathers the levels formed by a batched product with
+      // FULL_ITEM_MULT times larger items; the initial pass and FP64 iterates use the chunk
+      const LevelDev& L = a.dd.lv[s.level];
+      const int ch = dyn && sizeof(VT) == 4 && (level_structured(L.kind) || L.tc) ? chunk * FULL_ITEM_MULT : chunk;
+      items = s.done ? 0 : (s.n_kept + ch - 1) / ch;
     }
     // block exclusive scan of items
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -836,10 +850,11 @@ __global__ void __launch_bounds__(CORR_THREADS, 4) k_corr_pass(PassArgs<VT> a) {
     const int chunk = item - a.offsets[b];
     const SigState& s = a.st[b];
     const LevelDev& L = a.dd.lv[s.level];
-    const int p0 = chunk * CH, p1 = min(s.n_kept, p0 + CH);
+    const bool from_full = level_structured(L.kind) || L.tc;
+    const int CHs = from_full ? CH * FULL_ITEM_MULT : CH;   // gathers take larger items
+    const int p0 = chunk * CHs, p1 = min(s.n_kept, p0 + CHs);
     const VT* rho = a.Rho + (int64_t)b * a.ldN;
     const float nrho_f = s.nrho_ru, thr_f = s.thr_f, beta_f = s.beta_f;
-    const bool from_full = level_structured(L.kind) || L.tc;
     const bool tight = !from_full && L.kind == LK_F32 && s.corr_tight;
     const float dq_f = L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
     const float gt_f = tight ? __double2float_ru(L.gam_tight) : 0.f;
@@ -864,9 +879,21 @@ __global__ void __launch_bounds__(CORR_THREADS, 4) k_corr_pass(PassArgs<VT> a) {
       G[pos] = (VT)g;
     };
     if (from_full) {
-      for (int pos = p0 + (int)threadIdx.x; pos < p1; pos += CORR_THREADS) {
-        const int32_t j = kp[pos];
-        update(pos, j, a.Gfull[(int64_t)b * a.K + j]);
+      // four positions per thread at a time: their loads are issued before any update stores
+      const float* gf = a.Gfull + (int64_t)b * a.K;
+      for (int pos0 = p0 + (int)threadIdx.x; pos0 < p1; pos0 += 4 * CORR_THREADS) {
+        int32_t jv[4];
+        float gv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int pos = pos0 + u * CORR_THREADS;
+          jv[u] = pos < p1 ? kp[pos] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) gv[u] = jv[u] >= 0 ? gf[jv[u]] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (jv[u] >= 0) update(pos0 + u * CORR_THREADS, jv[u], gv[u]);
       }
     } else if (tight) {
       // error-free products (Dot2) with their tight bound, near the end of the signal's solve
@@ -1191,6 +1218,10 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
     if (pe.cert <= a.sp.tol) {
       s.corr_tight = 1;
       s.refine = may_stop ? 1 : 0;
+      if (s.refine) {
+        s.e_wm = 0.0;   // k_refine's blocks combine their maxima into it
+        a.refine_list[atomicAdd(&a.counters[3], 1)] = b;
+      }
     }
   }
   if (!s.refine) {
@@ -1206,57 +1237,63 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
 
 // Tightening of the certificate on the exact FP32 level (requested by k_eval when the gap
 // without the bulk pass's rounding margins already meets tol): the atoms that can attain the
-// maximum -- those whose loose upper bound exceeds max_j |g^_j|, every other atom being below
-// that maximum -- are recomputed from the FP32 data with error-free products.  One block per
-// signal; the lanes test 32 positions at once, the warp recomputes each candidate.
+// maximum, |g^_j| + bound_j > max |g^|, are recomputed with error-free products.  k_eval lists
+// the refining signals (refine_list, counters[3]); each is split into REFINE_SPLIT items, item
+// p scanning the 32-atom windows p * 8 + w (mod REFINE_SPLIT * 8) of the preserved list with
+// warp w.  The lanes test 32 positions at once and the warp recomputes each candidate; the
+// items of a signal combine their maxima in e_wm (zeroed by k_eval) with an atomic maximum on
+// the bit pattern, which orders non-negative doubles as their values.
+constexpr int REFINE_SPLIT = 8;
+
 template <typename VT>
 __global__ void __launch_bounds__(256) k_refine(PassArgs<VT> a) {
-  const int b = blockIdx.x;
-  SigState* sp = a.st + b;
-  __shared__ int s_go;
-  __shared__ double s_wmax[8];
-  if (threadIdx.x == 0) s_go = !sp->done && sp->refine;
-  __syncthreads();
-  if (!s_go) return;
   if constexpr (sizeof(VT) == 4) {
+    __shared__ double s_wmax[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const SigState& s = *sp;
-    const LevelDev& L = a.dd.lv[s.level];
-    const int n_kept = s.n_kept;
-    const int32_t* kp = kept_of(a, b, s.parity);
-    const VT* G = a.G + (int64_t)b * a.K;
-    const double T = s.e_m2, nrho = sqrt(s.rr);
-    const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
-    const float T_f = __double2float_rd(T);
-    // |g^_j - a_j^T rho| <= epsr_j ||rho|| (+ kappa_j dq for a quantised operand) + 3 u |g^_j|
-    const float nr_f = __double2float_ru(nrho);
-    const float dq_f = L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
-    double wm = 0.0;
-    for (int base = wid * 32; base < n_kept; base += 256) {
-      const int pos = base + lane;
-      int32_t j = 0;
-      bool cand = false;
-      if (pos < n_kept) {
-        j = kp[pos];
-        float ub = __fmaf_ru(L.epsr32[j], nr_f, __fmul_ru(fabsf((float)G[pos]), 1.0000004f));
-        if (dq_f > 0.f) ub = __fmaf_ru(L.kappa32[j], dq_f, ub);
-        cand = ub > T_f;
+    const int total = a.counters[3] * REFINE_SPLIT;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+      const int b = a.refine_list[item / REFINE_SPLIT];
+      const int part = item % REFINE_SPLIT;
+      SigState* sp = a.st + b;
+      const SigState& s = *sp;
+      const LevelDev& L = a.dd.lv[s.level];
+      const int n_kept = s.n_kept;
+      const int32_t* kp = kept_of(a, b, s.parity);
+      const VT* G = a.G + (int64_t)b * a.K;
+      const double T = s.e_m2, nrho = sqrt(s.rr);
+      const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
+      const float T_f = __double2float_rd(T);
+      // |g^_j - a_j^T rho| <= epsr_j ||rho|| (+ kappa_j dq for a quantised operand) + 3 u |g^_j|
+      const float nr_f = __double2float_ru(nrho);
+      const float dq_f = L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
+      double wm = 0.0;
+      for (int base = (part * 8 + wid) * 32; base < n_kept; base += REFINE_SPLIT * 256) {
+        const int pos = base + lane;
+        int32_t j = 0;
+        bool cand = false;
+        if (pos < n_kept) {
+          j = kp[pos];
+          float ub = __fmaf_ru(L.epsr32[j], nr_f, __fmul_ru(fabsf((float)G[pos]), 1.0000004f));
+          if (dq_f > 0.f) ub = __fmaf_ru(L.kappa32[j], dq_f, ub);
+          cand = ub > T_f;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, cand);
+        while (m) {
+          const int l = __ffs(m) - 1;
+          m &= m - 1;
+          const int64_t jj = __shfl_sync(0xffffffffu, j, l);
+          const double g = warp_atom_dot(L, jj, (int)a.ldN, rho, nullptr, lane);
+          wm = fmax(wm, fabs(g) * (1.0 + 3.0 * U32) + L.gam_tight * L.kappa[jj] * nrho);
+        }
       }
-      unsigned m = __ballot_sync(0xffffffffu, cand);
-      while (m) {
-        const int l = __ffs(m) - 1;
-        m &= m - 1;
-        const int64_t jj = __shfl_sync(0xffffffffu, j, l);
-        const double g = warp_atom_dot(L, jj, (int)a.ldN, rho, nullptr, lane);
-        wm = fmax(wm, fabs(g) * (1.0 + 3.0 * U32) + L.gam_tight * L.kappa[jj] * nrho);
+      if (lane == 0) s_wmax[wid] = wm;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < 8; ++w) m = fmax(m, s_wmax[w]);
+        if (m > 0.0) atomicMax(reinterpret_cast<unsigned long long*>(&sp->e_wm), (unsigned long long)__double_as_longlong(m));
       }
-    }
-    if (lane == 0) s_wmax[wid] = wm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double m = 0.0;
-      for (int w = 0; w < 8; ++w) m = fmax(m, s_wmax[w]);
-      sp->e_wm = m;
+      __syncthreads();
     }
   }
 }
@@ -1613,13 +1650,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_full_check(PassArgs<VT> a) {
   const int CH = a.sp.chunk;
   const LevelDev& L = a.dd.lv[a.dd.n_levels - 1];
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    int lo = 0, hi = B - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (a.offsets2[mid] <= item) lo = mid;
-      else hi = mid - 1;
-    }
-    const int b = lo;
+    const int b = item_signal(a.offsets2, 0, B - 1, item);
     const int chunk = item - a.offsets2[b];
     const SigState& s = a.st[b];
     const VT* rho = a.Rho + (int64_t)b * a.ldN;
@@ -2244,7 +2275,7 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
   k_eval<VT, 0><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa);
   if constexpr (sizeof(VT) == 4) {
-    k_refine<VT><<<B, 256, 0, st>>>(pa);
+    k_refine<VT><<<(unsigned)(num_sms() * 4), 256, 0, st>>>(pa);
     k_eval<VT, 1><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa);
   }
   k_screen<VT><<<B, SCREEN_THREADS, 0, st>>>(pa);
@@ -2785,9 +2816,10 @@ static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
     int rc = dict_prepare(d, 0.0);
     if (rc) return rc;
   }
-  // FP32 iterates cannot carry a certificate much below 1e-7: the duality gap of the dynamic dual
-  // point is first order in the point's rounding (about 6e-8 relative).  Tighter tolerances on
-  // an FP32 dictionary run the FP64-accumulation rung with FP64 iterates (as final_fp64 does).
+  // An FP32 point cannot carry a certificate much below 1e-7: the duality gap of the dynamic dual
+  // point is first order in the point's rounding (about 6e-8 relative), and on the 2048 x 8192
+  // batch a quarter of the signals stall above tol = 1e-7.  Tolerances below 5e-7 on an FP32
+  // dictionary run the FP64-accumulation rung with FP64 iterates (as final_fp64 does).
   if (d->exact_kind == LK_F32 && io.tol < FP32_TOL_FLOOR && !io.point_f32) io.opts.final_fp64 = 1;
   const bool vt_double = d->exact_kind == LK_F64 || io.opts.final_fp64;
   Workspace* w = nullptr;
