@@ -113,11 +113,9 @@ struct SigState {
   float thr_f, beta_f;               // lam / L and the FISTA momentum, as FP32 (update of the pass)
   float c_nrho_ru;                   // ||rho^|| of the snapshot, rounded up
   unsigned pm1, pm2;                 // per-pass maxima of the correlation (FP32 bit patterns, >= 0)
-  double e_m1, e_m2;                 // the pass's maxima as evaluated (kept for the refinement)
-  double e_wm;                       // refinement: max over the recomputed candidates (tight bounds)
   // screening scalars of the pass: |s'|, |s'| ||rho||, test radius, |s~|, R~, 1 / lam
   double t_abs_sp, t_c_eps, t_Rs, t_abs_st, t_Rt, t_inv_lam;
-  int act, scr, snap, refine;        // outcome of the pass, screen flag, snapshot, tighten request
+  int act, scr, snap;                // outcome of the pass, screen flag, snapshot
   int res_tight, c_res_tight;        // residual with error-free products (next passes, sticky / the snapshot)
   int corr_tight;                    // exact level: correlations with error-free products (sticky)
   int res_used;                      // the products the current pass's residual was formed with

@@ -50,8 +50,7 @@ struct Workspace {
   double* part_res = nullptr;        // B x nrb x 2
   double* part_corr = nullptr;       // B x nch x 2
   int32_t* offsets = nullptr;        // B + 1
-  int32_t* refine_list = nullptr;    // B: signals whose certificate k_refine tightens this pass
-  int32_t* counters = nullptr;       // [0] done count, [1] stop flag, [2] chunk, [3] refine count,
+  int32_t* counters = nullptr;       // [0] done count, [1] stop flag, [2] chunk,
                                      // [8 + l] signals on tensor-core level l
   double* alg_bytes = nullptr;       // [6] algorithmic bytes per kernel kind
   SigState* st = nullptr;
@@ -77,8 +76,7 @@ void free_ws(Workspace* w) {
   if (!w) return;
   void* ptrs[] = {w->Yw, w->Rho, w->X, w->Z, w->G, w->Xout, w->nz_val, w->nz_idx, w->kept, w->c0ub,
                   w->mask, w->cand_idx, w->cand_val, w->offsets2, w->part_full,
-                  w->part_res, w->part_corr, w->offsets, w->refine_list, w->counters, w->alg_bytes, w->st, w->Gfull,
-                  w->AZ, w->Xd, w->Tk,
+                  w->part_res, w->part_corr, w->offsets, w->counters, w->alg_bytes, w->st, w->Gfull, w->AZ, w->Xd, w->Tk,
                   w->Fs};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < MAX_LEVELS; ++l) {
@@ -146,7 +144,6 @@ static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
   rc |= ws_alloc((void**)&w->part_res, (size_t)B * w->nrb * 2 * 8);
   rc |= ws_alloc((void**)&w->part_corr, (size_t)B * w->nch * 2 * 8);
   rc |= ws_alloc((void**)&w->offsets, (size_t)(B + 1) * 4);
-  rc |= ws_alloc((void**)&w->refine_list, (size_t)B * 4);
   rc |= ws_alloc((void**)&w->counters, 64);
   rc |= ws_alloc((void**)&w->alg_bytes, 16 * sizeof(double));   // [0,6) bytes, [8,16) atom-passes per level
   rc |= ws_alloc((void**)&w->st, (size_t)B * sizeof(SigState));
@@ -200,7 +197,6 @@ struct PassArgs {
   double* part_res;
   double* part_corr;
   int32_t* offsets;
-  int32_t* refine_list;
   int32_t* counters;
   double* alg_bytes;
   SigState* st;
@@ -253,7 +249,6 @@ static void fill_pass_args(PassArgs<VT>& pa, Workspace* w, const lasso_dict* d) 
   pa.part_res = w->part_res;
   pa.part_corr = w->part_corr;
   pa.offsets = w->offsets;
-  pa.refine_list = w->refine_list;
   pa.counters = w->counters;
   pa.alg_bytes = w->alg_bytes;
   pa.st = w->st;
@@ -348,10 +343,7 @@ __global__ void k_schedule(PassArgs<VT> a, int dyn) {
   int done_total = 0;
   __syncthreads();
   const int chunk = s_chunk;
-  if (threadIdx.x == 0) {
-    a.counters[2] = chunk;
-    a.counters[3] = 0;     // the next pass's k_eval lists the signals k_refine tightens
-  }
+  if (threadIdx.x == 0) a.counters[2] = chunk;
   for (int base = 0; base < B; base += blockDim.x) {
     int b = base + threadIdx.x;
     int items = 0, dn = 0;
@@ -1083,7 +1075,7 @@ __device__ __forceinline__ void apply_scalars(SigState& s, const PassScalars& ps
 // Outcome of the pass for one signal once its certificate is known: stop (converged, or an
 // error), snapshot the point for the full-dictionary check, or continue; and the scalars of the
 // screening test.  m1_bulk: the pass's own maximum (finiteness check); m1_used: the one the
-// certificate used (tightened by the refinement).
+// certificate used.
 template <typename VT>
 __device__ void pass_decide(SigState& s, const PassArgs<VT>& a, double m1_bulk, double m1_used,
                             const PassScalars& ps) {
@@ -1160,29 +1152,15 @@ __device__ __forceinline__ void check_stall(SigState& s, const PassArgs<VT>& a, 
 }
 
 // FP64 scalars of the pass, one thread per signal (FP64 issue is shared by the 32 signals of a
-// warp instead of one): the certificate, the pass count, and either the outcome of the pass or,
-// on the exact FP32 level near convergence, the request to tighten the certificate (k_screen).
-template <typename VT, int FINISH>
+// warp instead of one): the certificate, the pass count and the outcome of the pass; on the
+// exact FP32 level near convergence, the switch of the signal's correlations to error-free
+// products (k_corr_pass, from the next pass on).
+template <typename VT>
 __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.sp.B) return;
   SigState* sp = a.st + b;
   if (sp->done) return;
-  if (FINISH) {
-    // the certificate with the recomputed candidates (k_refine): max(max |g^|, tight bounds),
-    // never above the bulk bound
-    if (!sp->refine) return;
-    SigState s = *sp;
-    const LevelDev& L = a.dd.lv[s.level];
-    const double m1 = fmin(fmax(s.e_m2, s.e_wm), s.e_m1);
-    const PassScalars ps = pass_scalars<VT>(s, L, s.rr, s.yr, m1, s.e_m2);
-    apply_scalars(s, ps);
-    pass_decide<VT>(s, a, s.e_m1, m1, ps);
-    check_stall<VT>(s, a, ps.cert);
-    s.refine = 0;
-    *sp = s;
-    return;
-  }
   SigState s = *sp;
   const LevelDev& L = a.dd.lv[s.level];
   const int I = a.dd.n_levels - 1;
@@ -1204,30 +1182,15 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
   s.iters += 1;
   s.level_passes[s.level] += 1;
   if (a.alg_bytes) atomicAdd(&a.alg_bytes[8 + s.level], (double)s.n_kept);
-  s.e_m1 = m1;
-  s.e_m2 = m2;
-  s.refine = 0;
-  // (with the full-dictionary stop, only a pass that may take a snapshot needs the tight value)
-  const bool may_stop = !a.sp.full_gap || (!s.pending && s.iters >= s.next_check);
   if (sizeof(VT) == 4 && L.kind == LK_F32 && !L.tc && s.level == I && ps.cert > a.sp.tol && rr > 0.0 &&
       m2 > 0.0 && !s.corr_tight) {
     // would the certificate meet tol with the tight products?  then the next passes compute the
-    // correlations with error-free products (sticky), and k_refine tightens this one if a
-    // snapshot may follow
+    // correlations with error-free products (sticky)
     const PassScalars pe = pass_scalars<VT>(s, L, rr, yr, m2 * (1.0 + 3.0 * U32), m2);
-    if (pe.cert <= a.sp.tol) {
-      s.corr_tight = 1;
-      s.refine = may_stop ? 1 : 0;
-      if (s.refine) {
-        s.e_wm = 0.0;   // k_refine's blocks combine their maxima into it
-        a.refine_list[atomicAdd(&a.counters[3], 1)] = b;
-      }
-    }
+    if (pe.cert <= a.sp.tol) s.corr_tight = 1;
   }
-  if (!s.refine) {
-    pass_decide<VT>(s, a, m1, m1, ps);
-    check_stall<VT>(s, a, ps.cert);
-  }
+  pass_decide<VT>(s, a, m1, m1, ps);
+  check_stall<VT>(s, a, ps.cert);
   // the next residuals with error-free products once the certificate nears tol, or once the
   // fast residual's rounding bound is a visible part of it (sticky)
   if (!s.res_tight && s.level == I && (ps.cert <= 30.0 * a.sp.tol || ps.delta >= 0.1 * (ps.Gp + ps.delta)))
@@ -1235,71 +1198,7 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
   *sp = s;
 }
 
-// Tightening of the certificate on the exact FP32 level (requested by k_eval when the gap
-// without the bulk pass's rounding margins already meets tol): the atoms that can attain the
-// maximum, |g^_j| + bound_j > max |g^|, are recomputed with error-free products.  k_eval lists
-// the refining signals (refine_list, counters[3]); each is split into REFINE_SPLIT items, item
-// p scanning the 32-atom windows p * 8 + w (mod REFINE_SPLIT * 8) of the preserved list with
-// warp w.  The lanes test 32 positions at once and the warp recomputes each candidate; the
-// items of a signal combine their maxima in e_wm (zeroed by k_eval) with an atomic maximum on
-// the bit pattern, which orders non-negative doubles as their values.
-constexpr int REFINE_SPLIT = 8;
-
-template <typename VT>
-__global__ void __launch_bounds__(256) k_refine(PassArgs<VT> a) {
-  if constexpr (sizeof(VT) == 4) {
-    __shared__ double s_wmax[8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int total = a.counters[3] * REFINE_SPLIT;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-      const int b = a.refine_list[item / REFINE_SPLIT];
-      const int part = item % REFINE_SPLIT;
-      SigState* sp = a.st + b;
-      const SigState& s = *sp;
-      const LevelDev& L = a.dd.lv[s.level];
-      const int n_kept = s.n_kept;
-      const int32_t* kp = kept_of(a, b, s.parity);
-      const VT* G = a.G + (int64_t)b * a.K;
-      const double T = s.e_m2, nrho = sqrt(s.rr);
-      const float* rho = reinterpret_cast<const float*>(a.Rho + (int64_t)b * a.ldN);
-      const float T_f = __double2float_rd(T);
-      // |g^_j - a_j^T rho| <= epsr_j ||rho|| (+ kappa_j dq for a quantised operand) + 3 u |g^_j|
-      const float nr_f = __double2float_ru(nrho);
-      const float dq_f = L.tc ? __double2float_ru(s.dq * 1.001) : 0.f;
-      double wm = 0.0;
-      for (int base = (part * 8 + wid) * 32; base < n_kept; base += REFINE_SPLIT * 256) {
-        const int pos = base + lane;
-        int32_t j = 0;
-        bool cand = false;
-        if (pos < n_kept) {
-          j = kp[pos];
-          float ub = __fmaf_ru(L.epsr32[j], nr_f, __fmul_ru(fabsf((float)G[pos]), 1.0000004f));
-          if (dq_f > 0.f) ub = __fmaf_ru(L.kappa32[j], dq_f, ub);
-          cand = ub > T_f;
-        }
-        unsigned m = __ballot_sync(0xffffffffu, cand);
-        while (m) {
-          const int l = __ffs(m) - 1;
-          m &= m - 1;
-          const int64_t jj = __shfl_sync(0xffffffffu, j, l);
-          const double g = warp_atom_dot(L, jj, (int)a.ldN, rho, nullptr, lane);
-          wm = fmax(wm, fabs(g) * (1.0 + 3.0 * U32) + L.gam_tight * L.kappa[jj] * nrho);
-        }
-      }
-      if (lane == 0) s_wmax[wid] = wm;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < 8; ++w) m = fmax(m, s_wmax[w]);
-        if (m > 0.0) atomicMax(reinterpret_cast<unsigned long long*>(&sp->e_wm), (unsigned long long)__double_as_longlong(m));
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// One block per signal, after the pass has been evaluated (k_eval, and k_refine for a tightened
-// certificate).  In one sweep of the preserved list, every atom is tested (stable GAP or Dynamic Safe
+// One block per signal, after the pass has been evaluated (k_eval).  In one sweep of the preserved list, every atom is tested (stable GAP or Dynamic Safe
 // sphere), K_t is counted, and the preserved list and the nonzero list of z+ are compacted in
 // order; Algorithm 2 picks the next level and the sums of the nonzero list close the pass.
 // FP32 iterates keep the per-atom work in FP32: tests rounded upward (over-estimating only
@@ -1657,7 +1556,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_full_check(PassArgs<VT> a) {
     const uint8_t* mk = a.mask + (int64_t)b * a.K;
     const float nrho_f = s.c_nrho_ru;
     // an atom whose loose bound reaches the preserved atoms' maximum could decide the scaling:
-    // recompute it from the FP32 data with error-free products (tight bound), as k_refine does
+    // recompute it from the FP32 data with error-free products (tight bound)
     const bool tighten = sizeof(VT) == 4 && L.kind == LK_F32;
     const float T_f = __double2float_rd(s.c_m1);
     const int64_t j0 = (int64_t)chunk * CH, j1 = min((int64_t)a.K, j0 + CH);
@@ -2273,11 +2172,7 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   if constexpr (sizeof(VT) == 4) k_corr_pass<VT><<<corr_grid, CORR_THREADS, 0, st>>>(pa);
   else k_corr<VT, CORR_PASS><<<corr_grid, CORR_THREADS, corr_smem, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
-  k_eval<VT, 0><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa);
-  if constexpr (sizeof(VT) == 4) {
-    k_refine<VT><<<(unsigned)(num_sms() * 4), 256, 0, st>>>(pa);
-    k_eval<VT, 1><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa);
-  }
+  k_eval<VT><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(pa);
   k_screen<VT><<<B, SCREEN_THREADS, 0, st>>>(pa);
   if (pa.sp.full_gap) {
     k_schedule_full<VT><<<1, 1024, 0, st>>>(pa);
@@ -2297,7 +2192,7 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
 }
 
 static int pass_launches(bool has_kron, bool has_faust, bool full_gap, int n_tc, bool tc_full) {
-  return (has_kron ? 12 : 7) + (has_faust ? 2 : 0) + (full_gap ? (tc_full ? 5 : 3) : 0) + 2 * n_tc;
+  return (has_kron ? 10 : 5) + (has_faust ? 2 : 0) + (full_gap ? (tc_full ? 5 : 3) : 0) + 2 * n_tc;
 }
 
 // ------------------------------------------------------------------ autotuner
