@@ -50,7 +50,8 @@ struct Workspace {
   double* part_res = nullptr;        // B x nrb x 2
   double* part_corr = nullptr;       // B x nch x 2
   int32_t* offsets = nullptr;        // B + 1
-  int32_t* counters = nullptr;       // [0] done count, [1] stop flag, [2] chunk,
+  int32_t* live_list = nullptr;      // B: the signals still running, in order (k_schedule)
+  int32_t* counters = nullptr;       // [0] done count, [1] stop flag, [2] chunk, [4] live count,
                                      // [8 + l] signals on tensor-core level l
   double* alg_bytes = nullptr;       // [6] algorithmic bytes per kernel kind
   SigState* st = nullptr;
@@ -76,7 +77,8 @@ void free_ws(Workspace* w) {
   if (!w) return;
   void* ptrs[] = {w->Yw, w->Rho, w->X, w->Z, w->G, w->Xout, w->nz_val, w->nz_idx, w->kept, w->c0ub,
                   w->mask, w->cand_idx, w->cand_val, w->offsets2, w->part_full,
-                  w->part_res, w->part_corr, w->offsets, w->counters, w->alg_bytes, w->st, w->Gfull, w->AZ, w->Xd, w->Tk,
+                  w->part_res, w->part_corr, w->offsets, w->live_list, w->counters, w->alg_bytes, w->st, w->Gfull,
+                  w->AZ, w->Xd, w->Tk,
                   w->Fs};
   for (void* p : ptrs) cudaFree(p);
   for (int l = 0; l < MAX_LEVELS; ++l) {
@@ -144,6 +146,7 @@ static int get_ws(lasso_dict* d, int64_t B, bool vt_double, Workspace** out) {
   rc |= ws_alloc((void**)&w->part_res, (size_t)B * w->nrb * 2 * 8);
   rc |= ws_alloc((void**)&w->part_corr, (size_t)B * w->nch * 2 * 8);
   rc |= ws_alloc((void**)&w->offsets, (size_t)(B + 1) * 4);
+  rc |= ws_alloc((void**)&w->live_list, (size_t)B * 4);
   rc |= ws_alloc((void**)&w->counters, 64);
   rc |= ws_alloc((void**)&w->alg_bytes, 16 * sizeof(double));   // [0,6) bytes, [8,16) atom-passes per level
   rc |= ws_alloc((void**)&w->st, (size_t)B * sizeof(SigState));
@@ -197,6 +200,7 @@ struct PassArgs {
   double* part_res;
   double* part_corr;
   int32_t* offsets;
+  int32_t* live_list;
   int32_t* counters;
   double* alg_bytes;
   SigState* st;
@@ -249,6 +253,7 @@ static void fill_pass_args(PassArgs<VT>& pa, Workspace* w, const lasso_dict* d) 
   pa.part_res = w->part_res;
   pa.part_corr = w->part_corr;
   pa.offsets = w->offsets;
+  pa.live_list = w->live_list;
   pa.counters = w->counters;
   pa.alg_bytes = w->alg_bytes;
   pa.st = w->st;
@@ -423,6 +428,35 @@ __global__ void k_schedule(PassArgs<VT> a, int dyn) {
     }
     if (threadIdx.x == 0) a.counters[8 + l] = carry;
   }
+  // the live signals in order: the rows the per-signal kernels of the next pass walk
+  __syncthreads();
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < B; base += blockDim.x) {
+      const int b = base + threadIdx.x;
+      const bool on = b < B && !a.st[b].done;
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (lane == 0) sh_sum[wid] = __popc(bal);
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        int x = (int)threadIdx.x < nw ? sh_sum[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, x, o);
+          if ((int)threadIdx.x >= o) x += t;
+        }
+        sh_sum[threadIdx.x] = x;
+      }
+      __syncthreads();
+      if (on) a.live_list[carry + (wid ? sh_sum[wid - 1] : 0) + __popc(bal & ((1u << lane) - 1u))] = b;
+      __syncthreads();
+      if (threadIdx.x == 0) carry += sh_sum[nw - 1];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) a.counters[4] = carry;
+  }
 }
 
 // ------------------------------------------------------------------ residual (dense levels)
@@ -433,8 +467,7 @@ __global__ void k_schedule(PassArgs<VT> a, int dyn) {
 // Float iterates keep every per-row operation in FP32 (FP64 runs at 1/64 of the FP32 rate):
 // compensated (double-float) sums stand in for FP64 accumulators.
 template <typename VT>
-__global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
-  const int b = blockIdx.x;
+__device__ __forceinline__ void residual_signal(const PassArgs<VT>& a, int b) {
   SigState* sp = a.st + b;
   __shared__ int s_live;
   __shared__ int32_t s_idx[RES_THREADS];
@@ -635,6 +668,17 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
       const double vs = (double)sizeof(VT);
       atomicAdd(&a.alg_bytes[0], (double)nnz * ((double)N * level_elem_bytes(L.kind) + 4.0 + vs) + 2.0 * N * vs);
     }
+  }
+}
+
+// Over the live signals (k_schedule's list), one signal per block: launched with one block per
+// signal of the batch, the live signals take the first blocks and the hardware balances them.
+template <typename VT>
+__global__ void __launch_bounds__(RES_THREADS) k_residual(PassArgs<VT> a) {
+  const int n = a.counters[4];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    residual_signal<VT>(a, a.live_list[i]);
+    __syncthreads();
   }
 }
 
@@ -1204,10 +1248,9 @@ __global__ void __launch_bounds__(128) k_eval(PassArgs<VT> a) {
 // FP32 iterates keep the per-atom work in FP32: tests rounded upward (over-estimating only
 // keeps atoms), sum |z_j| compensated, sum eps_j |z_j| and sum kappa_j |z_j| rounded upward.
 template <typename VT>
-__global__ void __launch_bounds__(SCREEN_THREADS, 4) k_screen(PassArgs<VT> a) {
+__device__ __forceinline__ void screen_signal(const PassArgs<VT>& a, int b) {
   constexpr bool F32 = sizeof(VT) == 4;
   constexpr int NWS = SCREEN_THREADS / 32;
-  const int b = blockIdx.x;
   SigState* sp = a.st + b;
   __shared__ double sc[16];
   __shared__ int si[12];
@@ -1470,6 +1513,15 @@ __global__ void __launch_bounds__(SCREEN_THREADS, 4) k_screen(PassArgs<VT> a) {
   }
 }
 
+template <typename VT>
+__global__ void __launch_bounds__(SCREEN_THREADS, 4) k_screen(PassArgs<VT> a) {
+  const int n = a.counters[4];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    screen_signal<VT>(a, a.live_list[i]);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ full-dictionary check
 
 // Work items of the pending checks: ceil(K / chunk) per pending signal.
@@ -1588,8 +1640,7 @@ __global__ void __launch_bounds__(CORR_THREADS) k_full_check(PassArgs<VT> a) {
 // that level's error; a rejected atom whose bound reaches the preserved atoms' maximum is
 // recomputed from the exact data with error-free products.  One block per signal under check.
 template <typename VT>
-__global__ void __launch_bounds__(256) k_full_check_tc(PassArgs<VT> a, int lvl) {
-  const int b = blockIdx.x;
+__device__ __forceinline__ void full_check_tc_signal(const PassArgs<VT>& a, int lvl, int b) {
   const SigState& s = a.st[b];
   if (s.done || !s.pending) return;
   __shared__ double s_m[8];
@@ -1635,10 +1686,19 @@ __global__ void __launch_bounds__(256) k_full_check_tc(PassArgs<VT> a, int lvl) 
   for (int c = threadIdx.x; c < nchk; c += 256) a.part_full[(int64_t)b * a.nch + c] = c == 0 ? s_m[0] : 0.0;
 }
 
+// Over the signals under the check (k_schedule_full's slot list).
+template <typename VT>
+__global__ void __launch_bounds__(256) k_full_check_tc(PassArgs<VT> a, int lvl) {
+  const int n = a.counters[8 + FULL_SET];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    full_check_tc_signal<VT>(a, lvl, a.tc_list[(int64_t)FULL_SET * a.sp.B + i]);
+    __syncthreads();
+  }
+}
+
 // Full-dictionary gap of the snapshot point; stop (and return it) when it meets tol.
 template <typename VT>
-__global__ void k_full_finish(PassArgs<VT> a) {
-  const int b = blockIdx.x;
+__device__ __forceinline__ void full_finish_signal(const PassArgs<VT>& a, int b) {
   SigState* sp = a.st + b;
   __shared__ int s_stop, s_run;
   // one thread reads the flags (thread 0 rewrites the state below), so the whole block agrees
@@ -1681,6 +1741,15 @@ __global__ void k_full_finish(PassArgs<VT> a) {
   }
 }
 
+template <typename VT>
+__global__ void k_full_finish(PassArgs<VT> a) {
+  const int n = a.counters[8 + FULL_SET];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    full_finish_signal<VT>(a, a.tc_list[(int64_t)FULL_SET * a.sp.B + i]);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ tensor-core operand
 
 // Quantise rho^ of the signals on a tensor-core level into their slot rows of the GEMM operand
@@ -1690,8 +1759,7 @@ __global__ void k_full_finish(PassArgs<VT> a) {
 // bounds add.  The split level adds c2 ||r2|| for the product a2^T r2 it leaves out.  FP32
 // iterates: exact differences (BF16, split) or one rounding (E4M3), squares summed upward.
 template <typename VT>
-__global__ void __launch_bounds__(256) k_quant_rho(PassArgs<VT> a, int lvl, int fp8, int slot_set = -2) {
-  const int b = blockIdx.x;
+__device__ __forceinline__ void quant_rho_signal(const PassArgs<VT>& a, int lvl, int fp8, int slot_set, int b) {
   const int B = a.sp.B;
   // rows: the level's own slots (slot_set -2), every live signal in its own row (-1: the initial
   // pass, rho = y), or the slots of another list (the signals under the full-dictionary check)
@@ -1798,6 +1866,25 @@ __global__ void __launch_bounds__(256) k_quant_rho(PassArgs<VT> a, int lvl, int 
     if (fp8) L.rsig[b] = sg;
     // algorithmic work of the batched correlation of this signal: 2 N K flops per product
     if (a.alg_bytes) atomicAdd(&a.alg_bytes[5], (L.split ? 3.0 : 1.0) * 2.0 * (double)a.dd.N * (double)a.K);
+  }
+}
+
+// slot_set -1: every signal (the initial pass); otherwise over the slot list of level lvl (-2)
+// or of list slot_set.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_quant_rho(PassArgs<VT> a, int lvl, int fp8, int slot_set = -2) {
+  if (slot_set == -1) {
+    for (int b = blockIdx.x; b < a.sp.B; b += gridDim.x) {
+      quant_rho_signal<VT>(a, lvl, fp8, -1, b);
+      __syncthreads();
+    }
+    return;
+  }
+  const int set = slot_set == -2 ? lvl : slot_set;
+  const int n = a.counters[8 + set];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    quant_rho_signal<VT>(a, lvl, fp8, slot_set, a.tc_list[(int64_t)set * a.sp.B + i]);
+    __syncthreads();
   }
 }
 
@@ -2163,7 +2250,7 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   if (has_faust) k_faust_adj<VT><<<B, 256, 0, st>>>(pa);
   if (ev) cudaEventRecordWithFlags(ev[7], st, cudaEventRecordExternal);
   for (const TcJob& j : tc) {
-    k_quant_rho<VT><<<B, 256, 0, st>>>(pa, j.lvl, j.fp8);
+    k_quant_rho<VT><<<(unsigned)std::min<int64_t>(B, num_sms() * 4), 256, 0, st>>>(pa, j.lvl, j.fp8);
     tc_launch_corr(j.ops, pa.K, B, pa.ldN, j.scale, j.rsig, pa.tc_list + (int64_t)j.lvl * B, pa.counters + 8 + j.lvl,
                    pa.Gfull, tc_err, st);
   }
@@ -2177,14 +2264,15 @@ static void launch_pass(const PassArgs<VT>& pa, cudaStream_t st, bool has_kron, 
   if (pa.sp.full_gap) {
     k_schedule_full<VT><<<1, 1024, 0, st>>>(pa);
     if (full_job) {
-      k_quant_rho<VT><<<B, 256, 0, st>>>(pa, full_job->lvl, full_job->fp8, FULL_SET);
+      k_quant_rho<VT><<<(unsigned)std::min<int64_t>(B, num_sms() * 4), 256, 0, st>>>(pa, full_job->lvl,
+                                                                                 full_job->fp8, FULL_SET);
       tc_launch_corr(full_job->ops, pa.K, B, pa.ldN, full_job->scale, full_job->rsig,
                      pa.tc_list + (int64_t)FULL_SET * B, pa.counters + 8 + FULL_SET, pa.Gfull, tc_err, st);
-      k_full_check_tc<VT><<<B, 256, 0, st>>>(pa, full_job->lvl);
+      k_full_check_tc<VT><<<(unsigned)std::min<int64_t>(B, num_sms() * 4), 256, 0, st>>>(pa, full_job->lvl);
     } else {
       k_full_check<VT><<<corr_grid, CORR_THREADS, 0, st>>>(pa);
     }
-    k_full_finish<VT><<<B, 128, 0, st>>>(pa);
+    k_full_finish<VT><<<(unsigned)std::min<int64_t>(B, num_sms() * 8), 128, 0, st>>>(pa);
   }
   if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
   k_schedule<VT><<<1, 1024, 0, st>>>(pa, 1);
