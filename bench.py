@@ -45,8 +45,10 @@ def _args():
                     help="workload: c3 (default, the headline batched mixed-precision line) or c1 / c2 / c4 / c5")
     ap.add_argument("--grid", action="store_true",
                     help="run the Section V parameter grid instead (T/T_N, F/F_N per point)")
-    ap.add_argument("--grid-families", default="gaussian,kron,faust",
-                    help="comma list of grid families: gaussian, kron, faust")
+    ap.add_argument("--grid-families", default="gaussian,kron,faust,example,combos",
+                    help="comma list of grid families: gaussian, kron, faust, example (Section IV's worked "
+                         "example), combos (ISTA / FISTA x GAP / Dynamic Safe, single versus multiple "
+                         "approximations)")
     return ap.parse_args()
 
 
@@ -762,7 +764,8 @@ def run_grid(args):
     def work(st, rc):
         return sum(st.level_atoms[i] * rc[i] for i in range(len(rc)))
 
-    def point(family, d, d_exact, rc, Y, lmax, ratio, tol, algo=0, rule=0, Gamma=0.5, screened_exact=False):
+    def point(family, d, d_exact, rc, Y, lmax, ratio, tol, algo=0, rule=0, Gamma=0.5, screened_exact=False,
+              single=None):
         lam = torch.full((Y.shape[0],), ratio, dtype=torch.float64, device=dev) * lmax
         T, st, ok = timed(d, Y, lam, tol, algo=algo, rule=rule, Gamma=Gamma)
         TN, stn, okn = timed(d_exact, Y, lam, tol, algo=algo, rule=rule, screen_every=NO_SCREEN)
@@ -773,12 +776,56 @@ def run_grid(args):
                 "solved": ok, "solved_N": okn, "passes_max": st.passes, "passes_max_N": stn.passes,
                 "level_passes_per_signal": [v / Y.shape[0] for v in st.level_passes[:len(rc)]]}
         if screened_exact:
-            # the same screening on the exact dictionary alone (the paper's GAP Safe FISTA curve)
+            # the same screening on the exact dictionary alone (the paper's conventional-screening curve)
             TS, sts, oks = timed(d_exact, Y, lam, tol, algo=algo, rule=rule)
             line.update({"T_S_ms": 1e3 * TS, "T_S/T_N": TS / TN, "solved_S": oks})
+        if single is not None:
+            # a single approximation before the exact dictionary (the paper's single-approximation curve)
+            d1, rc1 = single
+            T1, st1, ok1 = timed(d1, Y, lam, tol, algo=algo, rule=rule, Gamma=Gamma)
+            line.update({"T_single_ms": 1e3 * T1, "T_single/T_N": T1 / TN, "F_single/F_N": work(st1, rc1) / max(FN, 1.0),
+                         "solved_single": ok1})
         print(json.dumps(line), flush=True)
 
     fams = set(args.grid_families.split(","))
+
+    if "example" in fams:
+        # Section IV's example: four approximations with RC = 0.15 (i + 1) (SuKro truncations to 5, 10,
+        # 15 and 20 terms of a 25-term sum, 0.03 per term), Gamma = 0.2, lambda / lambda_max = 0.2
+        we = S.paper_kron(0.85, n_signals=25, R=25)
+        Ye = torch.tensor(we.Y, dtype=torch.float32, device=dev)
+        de = pkg.Dictionary.kron(we.Bf, we.Cf)
+        for R in (5, 10, 15, 20):
+            de.add_level(pkg.LEVEL_KRON, R)
+        de.prepare()
+        dex = pkg.Dictionary.kron(we.Bf, we.Cf).prepare()
+        info = de.info()
+        print(json.dumps({"example": {"rc": info["rc"], "eps_mean": info["eps_mean"], "eps_max": info["eps_max"]}}),
+              flush=True)
+        lme = de.lambda_max(Ye)
+        point("example-sukro25-decay0.85", de, dex, info["rc"], Ye, lme, 0.2, 1e-6, Gamma=0.2, screened_exact=True)
+        de.close()
+        dex.close()
+    if "combos" in fams:
+        # single versus multiple approximations (Section V-B): FISTA / ISTA x GAP / Dynamic Safe on the
+        # moderate scenario, tol 1e-5, Gamma 0.5; multiple: R = 1, 2 truncations; single: R = 2 only
+        wm = S.paper_kron(0.5, n_signals=25)
+        Ym = torch.tensor(wm.Y, dtype=torch.float32, device=dev)
+        dm = pkg.Dictionary.kron(wm.Bf, wm.Cf).add_level(pkg.LEVEL_KRON, 1).add_level(pkg.LEVEL_KRON, 2).prepare()
+        d1 = pkg.Dictionary.kron(wm.Bf, wm.Cf).add_level(pkg.LEVEL_KRON, 2).prepare()
+        dmx = pkg.Dictionary.kron(wm.Bf, wm.Cf).prepare()
+        rcm, rc1 = dm.info()["rc"], d1.info()["rc"]
+        lmm = dm.lambda_max(Ym)
+        for algo in (0, 1):
+            for rule in (0, 1):
+                for ratio in ratios_grid:
+                    point("kron-decay0.5", dm, dmx, rcm, Ym, lmm, ratio, 1e-5, algo=algo, rule=rule, Gamma=0.5,
+                          screened_exact=True, single=(d1, rc1))
+        dm.close()
+        d1.close()
+        dmx.close()
+    if not fams & {"faust", "gaussian", "kron"}:
+        return 0
 
     if "faust" in fams:
         # the source-localisation stand-in: four sparse-factor levels, or only the finest one

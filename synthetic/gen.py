@@ -38,7 +38,7 @@ __all__ = [
 ]
 
 _CFG = {"c1": 1, "c2": 2, "c3": 3, "c4": 4, "c5": 5, "dense_small": 6, "kron_small": 7, "ortho": 8,
-        "paper_dense": 9, "paper_kron": 10, "meg_faust": 11, "faust_small": 12}
+        "paper_dense": 9, "paper_kron": 10, "meg_faust": 11, "faust_small": 12, "paper_kron_example": 13}
 _DICT, _SIGNAL = 0, 1
 
 
@@ -273,13 +273,16 @@ def paper_dense(n_signals: int = 25, seed: int = 0, N: int = 2500, K: int = 1000
     return DenseWorkload("paper_dense", A, _f32(_unit_rows(Y)), ratios, 1e-6, sups, cfs)
 
 
-def paper_kron(decay: float, n_signals: int = 25, seed: int = 0) -> KronWorkload:
-    """The experiments' setting with a structured dictionary: A = (sum_{r<4} w_r B_r (x) C_r) diag(d),
+def paper_kron(decay: float, n_signals: int = 25, seed: int = 0, R: int = 4) -> KronWorkload:
+    """The experiments' setting with a structured dictionary: A = (sum_{r<R} w_r B_r (x) C_r) diag(d),
     B_r, C_r 50 x 100 (N = 2500, K = 10000), term weights w_r = decay^r (small decay: well approximated
-    by few terms, the paper's easy scenario; large decay: hard), unit-norm y = A x, x Bernoulli(0.02)."""
-    Bf, Cf = _kron_factors("paper_kron", 4, 50, 100, 50, 100, seed, decay)
-    Y, ratios, sups, cfs = _kron_signals("paper_kron", Bf, Cf, n_signals, seed, 0.02, None, False, fixed_ratio=1.0)
-    return KronWorkload(f"paper_kron-decay{decay}", Bf, Cf, _f32(_unit_rows(Y)), ratios, 1e-6, sups, cfs)
+    by few terms, the paper's easy scenario; large decay: hard), unit-norm y = A x, x Bernoulli(0.02).
+    R = 4 by default; the Section IV example uses more terms so that truncations to 5, 10, 15 and 20
+    of them (relative complexity 0.03 per term) form its four approximations."""
+    name = "paper_kron" if R == 4 else "paper_kron_example"
+    Bf, Cf = _kron_factors(name, R, 50, 100, 50, 100, seed, decay)
+    Y, ratios, sups, cfs = _kron_signals(name, Bf, Cf, n_signals, seed, 0.02, None, False, fixed_ratio=1.0)
+    return KronWorkload(f"{name}{R}-decay{decay}", Bf, Cf, _f32(_unit_rows(Y)), ratios, 1e-6, sups, cfs)
 
 
 # ----------------------------------------------------------------------------- sparse-factor products
