@@ -225,6 +225,11 @@ typedef struct {
     int64_t fp64_resolved;   /* signals solved again with FP64 iterates (opts.fp64_fallback)     */
     int64_t corr_chunk;      /* atoms per correlation work item used by the solve              */
     int64_t corr_blocks_per_sm; /* correlation grid, in blocks per SM                           */
+    double level_rc[8];      /* relative complexity each level of the solve's ladder used in
+                                Algorithm 2: measured for the tensor-core levels (time per signal
+                                of the batched product over every atom / that of the exact
+                                level's gather over every atom, once per batch size class), else
+                                the level's RC (lasso_dict_set_rc, or the byte / FLOP ratio)    */
 } lasso_stats;
 
 /* Solve one signal with FastL1 (Algorithm 1: FISTA / ISTA on the preserved atoms, stable safe

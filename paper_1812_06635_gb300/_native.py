@@ -52,6 +52,7 @@ class LassoStats(C.Structure):
         ("fp64_resolved", C.c_int64),
         ("corr_chunk", C.c_int64),
         ("corr_blocks_per_sm", C.c_int64),
+        ("level_rc", C.c_double * 8),
     ]
 
 

@@ -64,7 +64,15 @@ struct lasso_dict {
   lasso::HostLevel rung64;             // FP64-accumulation rung on FP32 exact data (lazy)
   double L = 0.0;
   bool prepared = false;
-  std::map<int, std::pair<int, int>> corr_tune;   // log2(B) class -> (chunk, blocks per SM)
+  // per batch size class (log2 B): the correlation pass's chunk and blocks per SM, the exact level's
+  // measured time per (signal, atom) product in ns, and the measured relative complexity of every
+  // tensor-core level of the solve's ladder (index of the level; -1 where not measured)
+  struct CorrTune {
+    int chunk = 0, bps = 0;
+    double exact_ns = 0.0;
+    std::vector<double> rc;
+  };
+  std::map<int, CorrTune> corr_tune;
   lasso::Workspace* ws = nullptr;     // FP32-iterate solves
   lasso::Workspace* ws64 = nullptr;   // FP64-iterate solves
 };

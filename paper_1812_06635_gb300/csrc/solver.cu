@@ -2319,8 +2319,8 @@ static int tune_corr(lasso_dict* d, const PassArgs<VT>& pa0, int64_t B, cudaStre
   while ((int64_t)1 << cls < B) ++cls;
   auto it = d->corr_tune.find(cls);
   if (it != d->corr_tune.end()) {
-    *chunk = it->second.first;
-    *bps = it->second.second;
+    *chunk = it->second.chunk;
+    *bps = it->second.bps;
     return LASSO_OK;
   }
   PassArgs<VT> pa = pa0;
@@ -2357,9 +2357,49 @@ static int tune_corr(lasso_dict* d, const PassArgs<VT>& pa0, int64_t B, cudaStre
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   LASSO_CUDA_TRY(cudaGetLastError());
-  d->corr_tune[cls] = std::make_pair(bc, bb);
+  lasso_dict::CorrTune& t = d->corr_tune[cls];
+  t.chunk = bc;
+  t.bps = bb;
+  t.exact_ns = 1e6 * (double)best / 3.0 / ((double)B * n_kept);   // per (signal, atom) product
   *chunk = bc;
   *bps = bb;
+  return LASSO_OK;
+}
+
+// Relative complexity of the tensor-core levels, measured (Section V-A measures RC rather than
+// deriving it): the time per signal of the level's batched product over every atom, over the
+// time per signal of the exact level's gather over every atom (its per-atom cost from tune_corr).
+// Measured once per dictionary and batch size class; a level whose RC the caller set keeps it.
+static int tune_tc_rc(lasso_dict* d, PassArgs<float>& pa, const std::vector<const HostLevel*>& order,
+                      const std::vector<TcJob>& jobs, int64_t B, cudaStream_t st, int* tc_err) {
+  int cls = 0;
+  while ((int64_t)1 << cls < B) ++cls;
+  auto it = d->corr_tune.find(cls);
+  if (it == d->corr_tune.end() || !(it->second.exact_ns > 0.0) || jobs.empty()) return LASSO_OK;
+  lasso_dict::CorrTune& t = it->second;
+  if ((int)t.rc.size() != pa.dd.n_levels) {
+    t.rc.assign(pa.dd.n_levels, -1.0);
+    cudaEvent_t e0, e1;
+    LASSO_CUDA_TRY(cudaEventCreate(&e0));
+    LASSO_CUDA_TRY(cudaEventCreate(&e1));
+    for (const TcJob& j : jobs) {
+      tc_launch_corr(j.ops, pa.K, B, pa.ldN, j.scale, j.rsig, nullptr, nullptr, pa.Gfull, tc_err, st);   // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 2; ++r)
+        tc_launch_corr(j.ops, pa.K, B, pa.ldN, j.scale, j.rsig, nullptr, nullptr, pa.Gfull, tc_err, st);
+      cudaEventRecord(e1, st);
+      LASSO_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      LASSO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      const double ns_signal = 1e6 * (double)ms / 2.0 / (double)B;
+      t.rc[j.lvl] = ns_signal / (t.exact_ns * (double)pa.K);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    LASSO_CUDA_TRY(cudaGetLastError());
+  }
+  for (int l = 0; l < pa.dd.n_levels; ++l)
+    if (t.rc[l] > 0.0 && !order[l]->rc_set) pa.dd.lv[l].rc = t.rc[l];
   return LASSO_OK;
 }
 
@@ -2448,6 +2488,8 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
       if (rc) return rc;
       pa.sp.chunk = c;
       corr_bps = g;
+      rc = tune_tc_rc(d, pa, order, tc_jobs, B, st, w->tc_err);
+      if (rc) return rc;
     }
   }
   const size_t vs = sizeof(VT);
@@ -2620,6 +2662,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     stats->launches = launches;
     stats->corr_chunk = pa.sp.chunk;
     stats->corr_blocks_per_sm = corr_bps;
+    for (int l = 0; l < pa.dd.n_levels && l < 8; ++l) stats->level_rc[l] = pa.dd.lv[l].rc;
     const int per_pass[6] = {1, 1, pa.sp.full_gap ? 4 : 1, 1, (has_kron ? 5 : 0) + (has_faust ? 2 : 0), 2 * (int)tc_jobs.size()};
     for (int q = 0; q < 6; ++q) {
       stats->kernel_launches[q] = replays * (int64_t)k * per_pass[q];

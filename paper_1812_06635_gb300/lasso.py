@@ -45,6 +45,7 @@ class Stats:
     fp64_resolved: int = 0
     corr_chunk: int = 0
     corr_blocks_per_sm: int = 0
+    level_rc: list = None
 
     KINDS = ("residual", "corr", "screen", "schedule", "kron", "tc_gemm")
 
@@ -54,7 +55,7 @@ class Stats:
                      float(s.lambda_), float(s.seconds), int(s.launches), [int(v) for v in s.kernel_launches],
                      [float(v) for v in s.kernel_ms], [float(v) for v in s.kernel_bytes],
                      [float(v) for v in s.level_atoms], int(s.fp64_resolved), int(s.corr_chunk),
-                     int(s.corr_blocks_per_sm))
+                     int(s.corr_blocks_per_sm), [float(v) for v in s.level_rc])
 
 
 def _ptr(a) -> C.c_void_p:
