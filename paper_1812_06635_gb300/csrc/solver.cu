@@ -52,7 +52,8 @@ struct Workspace {
   int32_t* offsets = nullptr;        // B + 1
   int32_t* live_list = nullptr;      // B: the signals still running, in order (k_schedule)
   int32_t* counters = nullptr;       // [0] done count, [1] stop flag, [2] chunk, [4] live count,
-                                     // [8 + l] signals on tensor-core level l
+                                     // [5] preserved atoms of the live signals, [8 + l] signals
+                                     // on tensor-core level l
   double* alg_bytes = nullptr;       // [6] algorithmic bytes per kernel kind
   SigState* st = nullptr;
   // Kronecker scratch
@@ -318,144 +319,144 @@ __global__ void k_init_state(PassArgs<VT> a, const double* __restrict__ lambdas)
   }
 }
 
-// Prefix sum of the correlation work items of the live signals, and the done count.
+// The schedule of the next pass, in one sweep over the batch (each signal's state read once):
+// the correlation work items of the live signals (prefix sums in offsets), the compacted list of
+// live signals, the slots of the live signals on each tensor-core level (the rows of that level's
+// quantised residual operand, so its GEMM covers only ceil(count / 256) signal tiles), the done
+// count, and the pass's chunk: the tuned one, halved (down to 32) while the preserved atoms of the
+// live signals would give fewer than two items per block (dyn; from the previous schedule's total).
 template <typename VT>
-__global__ void k_schedule(PassArgs<VT> a, int dyn) {
-  __shared__ int sh_sum[32];
-  __shared__ int sh_done[32];
-  __shared__ int carry, s_chunk;
+__global__ void __launch_bounds__(1024) k_schedule(PassArgs<VT> a, int dyn) {
+  constexpr int NW = 32;
+  __shared__ int w_items[NW], w_live[NW], w_lvl[MAX_LEVELS][NW];
+  __shared__ long long w_kept[NW];
+  __shared__ int t_items, t_live, t_lvl[MAX_LEVELS];
+  __shared__ long long t_kept;
+  __shared__ int c_items, c_live, c_lvl[MAX_LEVELS];
+  __shared__ long long c_kept;
   const int B = a.sp.B;
-  // atoms per correlation work item: the tuned chunk, halved (down to 32) while the live
-  // signals' preserved atoms would give fewer than two items per block of the pass (dyn)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nl = a.dd.n_levels;
+  int chunk = a.sp.chunk;
   if (dyn && sizeof(VT) == 4) {
-    long long ks = 0;
-    for (int b = threadIdx.x; b < B; b += blockDim.x)
-      if (!a.st[b].done) ks += a.st[b].n_kept;
-    for (int m = 16; m; m >>= 1) ks += __shfl_xor_sync(0xffffffffu, ks, m);
-    if ((threadIdx.x & 31) == 0) sh_sum[threadIdx.x >> 5] = (int)min(ks, (long long)INT_MAX);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      long long t = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh_sum[w];
-      int ch = a.sp.chunk;
-      while (ch > CORR_CHUNK && t / ch < 2LL * a.sp.corr_grid) ch >>= 1;
-      s_chunk = ch;
-    }
-  } else if (threadIdx.x == 0) {
-    s_chunk = a.sp.chunk;
+    const long long t = a.counters[5];
+    while (chunk > CORR_CHUNK && t / chunk < 2LL * a.sp.corr_grid) chunk >>= 1;
   }
-  if (threadIdx.x == 0) carry = 0;
-  int done_total = 0;
+  if (threadIdx.x == 0) {
+    c_items = c_live = 0;
+    c_kept = 0;
+    for (int l = 0; l < MAX_LEVELS; ++l) c_lvl[l] = 0;
+    a.counters[2] = chunk;
+  }
   __syncthreads();
-  const int chunk = s_chunk;
-  if (threadIdx.x == 0) a.counters[2] = chunk;
   for (int base = 0; base < B; base += blockDim.x) {
-    int b = base + threadIdx.x;
-    int items = 0, dn = 0;
+    const int b = base + threadIdx.x;
+    bool live = false;
+    int items = 0, lvl = -1;
+    long long nk = 0;
     if (b < B) {
       const SigState& s = a.st[b];
-      dn = s.done;
-      // the FP32 pass (k_corr_pass) gathers the levels formed by a batched product with
-      // FULL_ITEM_MULT times larger items; the initial pass and FP64 iterates use the chunk
-      const LevelDev& L = a.dd.lv[s.level];
-      const int ch = dyn && sizeof(VT) == 4 && (level_structured(L.kind) || L.tc) ? chunk * FULL_ITEM_MULT : chunk;
-      items = s.done ? 0 : (s.n_kept + ch - 1) / ch;
+      live = !s.done;
+      if (live) {
+        lvl = s.level;
+        nk = s.n_kept;
+        // the FP32 pass gathers the levels formed by a batched product with FULL_ITEM_MULT times
+        // larger items; the initial pass and FP64 iterates use the chunk
+        const LevelDev& L = a.dd.lv[lvl];
+        const int ch = dyn && sizeof(VT) == 4 && (level_structured(L.kind) || L.tc) ? chunk * FULL_ITEM_MULT : chunk;
+        items = (int)((nk + ch - 1) / ch);
+      }
     }
-    // block exclusive scan of items
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int v = items;
+    int v = items;   // inclusive warp scan of the items
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, v, o);
+      const int t = __shfl_up_sync(0xffffffffu, v, o);
       if (lane >= o) v += t;
     }
-    int dsum = warp_sum_i(dn);
-    if (lane == 31) sh_sum[wid] = v;
-    if (lane == 0) sh_done[wid] = dsum;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      int nw = blockDim.x >> 5;
-      int x = threadIdx.x < nw ? sh_sum[threadIdx.x] : 0;
+    long long kw = nk;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, x, o);
-        if ((int)threadIdx.x >= o) x += t;
-      }
-      sh_sum[threadIdx.x] = x;   // inclusive over warps
+    for (int m = 16; m; m >>= 1) kw += __shfl_xor_sync(0xffffffffu, kw, m);
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned bl = __ballot_sync(0xffffffffu, live);
+    unsigned bll[MAX_LEVELS];
+#pragma unroll
+    for (int l = 0; l < MAX_LEVELS; ++l) bll[l] = __ballot_sync(0xffffffffu, live && lvl == l);
+    if (lane == 31) w_items[wid] = v;
+    if (lane == 0) {
+      w_live[wid] = __popc(bl);
+      w_kept[wid] = kw;
+#pragma unroll
+      for (int l = 0; l < MAX_LEVELS; ++l) w_lvl[l][wid] = __popc(bll[l]);
     }
     __syncthreads();
-    int warp_off = wid ? sh_sum[wid - 1] : 0;
-    if (b < B) a.offsets[b] = carry + warp_off + v - items;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) done_total += sh_done[w];
+    if (wid == 0) {
+      // exclusive scans over the warps (one lane per warp) and the sweep's totals
+      const int nw = (int)(blockDim.x >> 5);
+      int xi = lane < nw ? w_items[lane] : 0, xl = lane < nw ? w_live[lane] : 0;
+      long long xk = lane < nw ? w_kept[lane] : 0;
+      int xv[MAX_LEVELS];
+#pragma unroll
+      for (int l = 0; l < MAX_LEVELS; ++l) xv[l] = lane < nw ? w_lvl[l][lane] : 0;
+      int si = xi, sl = xl, sv[MAX_LEVELS];
+#pragma unroll
+      for (int l = 0; l < MAX_LEVELS; ++l) sv[l] = xv[l];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int ti = __shfl_up_sync(0xffffffffu, si, o), tl = __shfl_up_sync(0xffffffffu, sl, o);
+        if (lane >= o) {
+          si += ti;
+          sl += tl;
+        }
+#pragma unroll
+        for (int l = 0; l < MAX_LEVELS; ++l) {
+          const int tv = __shfl_up_sync(0xffffffffu, sv[l], o);
+          if (lane >= o) sv[l] += tv;
+        }
+      }
+#pragma unroll
+      for (int m = 16; m; m >>= 1) xk += __shfl_xor_sync(0xffffffffu, xk, m);
+      if (lane < nw) {
+        w_items[lane] = si - xi;
+        w_live[lane] = sl - xl;
+#pragma unroll
+        for (int l = 0; l < MAX_LEVELS; ++l) w_lvl[l][lane] = sv[l] - xv[l];
+      }
+      if (lane == 31) {
+        t_items = si;
+        t_live = sl;
+#pragma unroll
+        for (int l = 0; l < MAX_LEVELS; ++l) t_lvl[l] = sv[l];
+      }
+      if (lane == 0) t_kept = xk;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) carry += sh_sum[(blockDim.x >> 5) - 1];
+    if (b < B) {
+      a.offsets[b] = c_items + w_items[wid] + v - items;
+      if (live) a.live_list[c_live + w_live[wid] + __popc(bl & lt)] = b;
+      for (int l = 0; l < nl; ++l) {
+        if (!a.dd.lv[l].tc) continue;
+        const bool on = live && lvl == l;
+        const int slot = c_lvl[l] + w_lvl[l][wid] + __popc(bll[l] & lt);
+        a.tc_slot[(int64_t)l * B + b] = on ? slot : -1;
+        if (on) a.tc_list[(int64_t)l * B + slot] = b;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      c_items += t_items;
+      c_live += t_live;
+      c_kept += t_kept;
+      for (int l = 0; l < MAX_LEVELS; ++l) c_lvl[l] += t_lvl[l];
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    a.offsets[B] = carry;
-    a.counters[0] = done_total;
-  }
-  // slots of the live signals on each tensor-core level: the rows of that level's quantised
-  // residual operand, so the batched GEMM covers only ceil(count / 256) signal tiles
-  for (int l = 0; l < a.dd.n_levels; ++l) {
-    if (!a.dd.lv[l].tc) continue;
-    __syncthreads();
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int base = 0; base < B; base += blockDim.x) {
-      const int b = base + threadIdx.x;
-      const bool on = b < B && !a.st[b].done && a.st[b].level == l;
-      const unsigned bal = __ballot_sync(0xffffffffu, on);
-      if (lane == 0) sh_sum[wid] = __popc(bal);
-      __syncthreads();
-      if (threadIdx.x < 32) {
-        int x = (int)threadIdx.x < nw ? sh_sum[threadIdx.x] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, x, o);
-          if ((int)threadIdx.x >= o) x += t;
-        }
-        sh_sum[threadIdx.x] = x;   // inclusive over warps
-      }
-      __syncthreads();
-      const int slot = carry + (wid ? sh_sum[wid - 1] : 0) + __popc(bal & ((1u << lane) - 1u));
-      if (b < B) a.tc_slot[(int64_t)l * B + b] = on ? slot : -1;
-      if (on) a.tc_list[(int64_t)l * B + slot] = b;
-      __syncthreads();
-      if (threadIdx.x == 0) carry += sh_sum[nw - 1];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) a.counters[8 + l] = carry;
-  }
-  // the live signals in order: the rows the per-signal kernels of the next pass walk
-  __syncthreads();
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int base = 0; base < B; base += blockDim.x) {
-      const int b = base + threadIdx.x;
-      const bool on = b < B && !a.st[b].done;
-      const unsigned bal = __ballot_sync(0xffffffffu, on);
-      if (lane == 0) sh_sum[wid] = __popc(bal);
-      __syncthreads();
-      if (threadIdx.x < 32) {
-        int x = (int)threadIdx.x < nw ? sh_sum[threadIdx.x] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, x, o);
-          if ((int)threadIdx.x >= o) x += t;
-        }
-        sh_sum[threadIdx.x] = x;
-      }
-      __syncthreads();
-      if (on) a.live_list[carry + (wid ? sh_sum[wid - 1] : 0) + __popc(bal & ((1u << lane) - 1u))] = b;
-      __syncthreads();
-      if (threadIdx.x == 0) carry += sh_sum[nw - 1];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) a.counters[4] = carry;
+    a.offsets[B] = c_items;
+    a.counters[0] = B - c_live;   // signals done
+    a.counters[4] = c_live;
+    a.counters[5] = (int)min(c_kept, (long long)INT_MAX);   // preserved atoms of the live signals
+    for (int l = 0; l < nl; ++l)
+      if (a.dd.lv[l].tc) a.counters[8 + l] = c_lvl[l];
   }
 }
 
