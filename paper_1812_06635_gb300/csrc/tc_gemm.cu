@@ -10,6 +10,7 @@
 //
 // Paper: the correlation A~^T rho of the proximal update (eq:ISTA_update) with the approximate
 // dictionaries of Section III; here batched over signals, which makes it a dense contraction.
+#include <algorithm>
 #include <cstring>
 
 #include <cudaTypedefs.h>
@@ -104,6 +105,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The signal of slot n0 + c0 + lane (lane's column of a 32-column chunk), its scale, and whether
+// the slot is live; the epilogue warps broadcast them by shuffle (no barrier among them).
+struct TcCol {
+  int on, sig;
+  float sigma;
+};
+__device__ __forceinline__ TcCol tc_col(int64_t slot, int64_t nslots, const int* __restrict__ list,
+                                        const float* __restrict__ sigma) {
+  TcCol c;
+  c.on = slot < nslots;
+  c.sig = c.on ? (list ? list[slot] : (int)slot) : 0;
+  c.sigma = c.on ? (sigma ? sigma[c.sig] : 1.f) : 0.f;
+  return c;
+}
+
+// Persistent over the tiles: CTA c takes tiles c, c + gridDim.x, ... of the (atom tile, signal
+// tile) grid of the live slots, atom tile fastest (consecutive CTAs share the signal tile's
+// residual rows in L2).  Two TMEM accumulators (512 columns): tile i accumulates in buffer i % 2
+// while the epilogue drains tile i - 1 from the other, and the TMA ring runs on across tiles.  A
+// launch with no live slot exits at once.
 template <int FP8>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb,
@@ -113,48 +138,36 @@ k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUten
           int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   __shared__ int s_fail;
-  __shared__ uint8_t s_on[TC_BN];
-  __shared__ float s_sigma[TC_BN];
-  __shared__ int s_sig[TC_BN];
   __shared__ uint32_t s_tmem;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;                                    // TC_STAGES x 16 KB
   uint8_t* sB = base + TC_STAGES * TC_BM * 128;          // TC_STAGES x 32 KB
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_BN * 128);
   uint64_t* empty = full + TC_STAGES;
-  uint64_t* accum = empty + TC_STAGES;
+  uint64_t* accf = empty + TC_STAGES;                    // [2]: tile in buffer b accumulated
+  uint64_t* acce = accf + 2;                             // [2]: buffer b drained by the epilogue
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
-  const int64_t n0 = (int64_t)blockIdx.y * TC_BN;
-
-  // ---- the tile's signal slots (uniform early exit past the count)
   const int64_t nslots = count ? (int64_t)*count : B;
-  if (n0 >= nslots) return;
-  if (threadIdx.x == 0) s_fail = 0;
-  for (int i = threadIdx.x; i < TC_BN; i += TC_THREADS) {
-    const int64_t slot = n0 + i;
-    const bool on = slot < nslots;
-    const int b = on ? (list ? list[slot] : (int)slot) : 0;
-    s_on[i] = on ? 1 : 0;
-    s_sig[i] = b;
-    s_sigma[i] = on ? (sigma ? sigma[b] : 1.f) : 0.f;
-  }
-  __syncthreads();
-
-  // ---- barriers and tensor memory
+  const int tm = (int)((K + TC_BM - 1) / TC_BM);
+  const int total = tm * (int)((nslots + TC_BN - 1) / TC_BN);
+  if ((int)blockIdx.x >= total) return;
   if (threadIdx.x == 0) {
+    s_fail = 0;
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    mbar_init(&accf[0], 1);
+    mbar_init(&accf[1], 1);
+    mbar_init(&acce[0], 4);
+    mbar_init(&acce[1], 4);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(TC_BN)
+                 "r"(2 * TC_BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -163,77 +176,104 @@ k_tc_corr(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUten
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   constexpr int KB_ELEMS = FP8 ? 128 : 64;   // elements per 128-byte K-slice
+  const int nk = nkb * nphase;               // phases: a^T r (1); a1^T r1, a1^T r2, a2^T r1 (3)
 
   if (warp == 0) {
-    // ---- TMA producer
+    // ---- TMA producer: the k-slices of every tile of this CTA, one ring
     if (lane == 0) {
-      // phases: a^T r (nphase 1); a1^T r1, a1^T r2, a2^T r1 (nphase 3)
-      const int nk = nkb * nphase;
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-        const int phase = kb / nkb, kk = kb - phase * nkb;
-        if (kb >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
-          s_fail = 1;
-          break;
+      int g = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < total && !stop; t += gridDim.x) {
+        const int64_t m0 = (int64_t)(t % tm) * TC_BM, n0 = (int64_t)(t / tm) * TC_BN;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % TC_STAGES;
+          const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
+          const int phase = kb / nkb, kk = kb - phase * nkb;
+          if (g >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+            s_fail = 1;
+            stop = true;
+            break;
+          }
+          mbar_expect_tx(&full[s], (uint32_t)(TC_BM + TC_BN) * 128u);
+          tma_load_2d(phase == 2 ? &tma2 : &tma, &full[s], sA + s * TC_BM * 128, kk * KB_ELEMS, (int)m0);
+          tma_load_2d(phase == 1 ? &tmb2 : &tmb, &full[s], sB + s * TC_BN * 128, kk * KB_ELEMS, (int)n0);
         }
-        mbar_expect_tx(&full[s], (uint32_t)(TC_BM + TC_BN) * 128u);
-        tma_load_2d(phase == 2 ? &tma2 : &tma, &full[s], sA + s * TC_BM * 128, kk * KB_ELEMS, (int)m0);
-        tma_load_2d(phase == 1 ? &tmb2 : &tmb, &full[s], sB + s * TC_BN * 128, kk * KB_ELEMS, (int)n0);
       }
     }
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = umma_idesc(FP8 ? 0u : 1u, TC_BM, TC_BN);
-      const int nk = nkb * nphase;
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-        if (!mbar_wait(&full[s], ph)) {
-          s_fail = 1;
-          break;
+      int g = 0, it = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < total && !stop; t += gridDim.x, ++it) {
+        const int buf = it & 1;
+        if (it >= 2) {
+          // the epilogue has drained this buffer's previous tile
+          if (!mbar_wait(&acce[buf], (uint32_t)((it >> 1) - 1) & 1u)) {
+            s_fail = 1;
+            break;
+          }
+          tc_fence_after();
         }
-        tc_fence_after();
-        const uint64_t ad = umma_sdesc(smem_u32(sA + s * TC_BM * 128));
-        const uint64_t bd = umma_sdesc(smem_u32(sB + s * TC_BN * 128));
+        const uint32_t dst = tmem + (uint32_t)(buf * TC_BN);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % TC_STAGES;
+          const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph)) {
+            s_fail = 1;
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = umma_sdesc(smem_u32(sA + s * TC_BM * 128));
+          const uint64_t bd = umma_sdesc(smem_u32(sB + s * TC_BN * 128));
 #pragma unroll
-        for (int k = 0; k < 4; ++k)   // four 32-byte K-steps per 128-byte slice
-          umma<FP8>(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
-        umma_commit(&empty[s]);
+          for (int k = 0; k < 4; ++k)   // four 32-byte K-steps per 128-byte slice
+            umma<FP8>(dst, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        if (!stop) umma_commit(&accf[buf]);   // arrives once the tile's MMAs have completed
       }
-      umma_commit(accum);   // arrives once every MMA issued above has completed
     }
   } else {
     // ---- epilogue: TMEM lane quarter (warp % 4) holds atoms m0 + 32 q .. + 31
     const int q = warp & 3;
-    const int64_t row = m0 + q * 32 + lane;
-    const bool ok = mbar_wait(accum, 0);
-    if (!ok) s_fail = 1;
-    tc_fence_after();
-    const float sc = row < K ? (scale ? scale[row] : 1.f) : 0.f;
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-      if (ok && row < K) {
+    int it = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+      const int buf = it & 1;
+      const int64_t m0 = (int64_t)(t % tm) * TC_BM, n0 = (int64_t)(t / tm) * TC_BN;
+      if (!mbar_wait(&accf[buf], (uint32_t)(it >> 1) & 1u)) {
+        s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      const int64_t row = m0 + q * 32 + lane;
+      const float sc = row < K ? (scale ? scale[row] : 1.f) : 0.f;
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        const TcCol mine = tc_col(n0 + c0 + lane, nslots, list, sigma);
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN + c0), r);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          if (s_on[c0 + i]) Gfull[(int64_t)s_sig[c0 + i] * K + row] = __uint_as_float(r[i]) * sc * s_sigma[c0 + i];
+          const int on = __shfl_sync(0xffffffffu, mine.on, i);
+          const int sig = __shfl_sync(0xffffffffu, mine.sig, i);
+          const float sg = __shfl_sync(0xffffffffu, mine.sigma, i);
+          if (on && row < K) Gfull[(int64_t)sig * K + row] = __uint_as_float(r[i]) * sc * sg;
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
   }
   if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // The same product with promoted accumulation.  The MMAs of k-block g (TC_GROUP consecutive
@@ -242,7 +282,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // warps load it with tcgen05.ld and add it to FP32 registers (round to nearest), then release the
 // buffer.  Warp 2 + e reads TMEM lane quarter (warp % 4) and the column half e / 4, so each
 // epilogue thread holds 128 running sums (one atom, 128 signals).  The tensor-core accumulation
-// chain is one k-block long; the k-block sums are added in FP32.
+// chain is one k-block long; the k-block sums are added in FP32.  Persistent over the tiles like
+// k_tc_corr; the k-block counter runs on across a CTA's tiles.
 template <int FP8>
 __global__ void __launch_bounds__(TCP_THREADS, 1)
 k_tc_corr_kb(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb,
@@ -252,9 +293,6 @@ k_tc_corr_kb(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CU
              int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   __shared__ int s_fail;
-  __shared__ uint8_t s_on[TC_BN];
-  __shared__ float s_sigma[TC_BN];
-  __shared__ int s_sig[TC_BN];
   __shared__ uint32_t s_tmem;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
@@ -265,21 +303,12 @@ k_tc_corr_kb(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CU
   uint64_t* acce = accf + 2;              // [2]: buffer b read by the 8 epilogue warps
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
-  const int64_t n0 = (int64_t)blockIdx.y * TC_BN;
   const int64_t nslots = count ? (int64_t)*count : B;
-  if (n0 >= nslots) return;
-  if (threadIdx.x == 0) s_fail = 0;
-  for (int i = threadIdx.x; i < TC_BN; i += TCP_THREADS) {
-    const int64_t slot = n0 + i;
-    const bool on = slot < nslots;
-    const int b = on ? (list ? list[slot] : (int)slot) : 0;
-    s_on[i] = on ? 1 : 0;
-    s_sig[i] = b;
-    s_sigma[i] = on ? (sigma ? sigma[b] : 1.f) : 0.f;
-  }
-  __syncthreads();
+  const int tm = (int)((K + TC_BM - 1) / TC_BM);
+  const int total = tm * (int)((nslots + TC_BN - 1) / TC_BN);
+  if ((int)blockIdx.x >= total) return;
   if (threadIdx.x == 0) {
+    s_fail = 0;
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
@@ -303,88 +332,110 @@ k_tc_corr_kb(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CU
   const uint32_t tmem = s_tmem;
   constexpr int KB_ELEMS = FP8 ? 128 : 64;
   const int nk = nkb * nphase;
-  const int ng = (nk + TC_GROUP - 1) / TC_GROUP;
+  const int ng = (nk + TC_GROUP - 1) / TC_GROUP;   // k-blocks per tile
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-        const int phase = kb / nkb, kk = kb - phase * nkb;
-        if (kb >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
-          s_fail = 1;
-          break;
+      int g = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < total && !stop; t += gridDim.x) {
+        const int64_t m0 = (int64_t)(t % tm) * TC_BM, n0 = (int64_t)(t / tm) * TC_BN;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % TC_STAGES;
+          const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
+          const int phase = kb / nkb, kk = kb - phase * nkb;
+          if (g >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+            s_fail = 1;
+            stop = true;
+            break;
+          }
+          mbar_expect_tx(&full[s], (uint32_t)(TC_BM + TC_BN) * 128u);
+          tma_load_2d(phase == 2 ? &tma2 : &tma, &full[s], sA + s * TC_BM * 128, kk * KB_ELEMS, (int)m0);
+          tma_load_2d(phase == 1 ? &tmb2 : &tmb, &full[s], sB + s * TC_BN * 128, kk * KB_ELEMS, (int)n0);
         }
-        mbar_expect_tx(&full[s], (uint32_t)(TC_BM + TC_BN) * 128u);
-        tma_load_2d(phase == 2 ? &tma2 : &tma, &full[s], sA + s * TC_BM * 128, kk * KB_ELEMS, (int)m0);
-        tma_load_2d(phase == 1 ? &tmb2 : &tmb, &full[s], sB + s * TC_BN * 128, kk * KB_ELEMS, (int)n0);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = umma_idesc(FP8 ? 0u : 1u, TC_BM, TC_BN);
-      for (int kb = 0; kb < nk; ++kb) {
-        const int g = kb / TC_GROUP;
-        const bool first = (kb % TC_GROUP) == 0;
-        const int buf = g & 1;
-        if (first && g >= 2) {
-          // the epilogue has read this buffer's previous k-block
-          if (!mbar_wait(&acce[buf], (uint32_t)((g >> 1) - 1) & 1u)) {
+      int g = 0, gb = 0;   // k-slice and k-block counters of this CTA
+      bool stop = false;
+      for (int t = blockIdx.x; t < total && !stop; t += gridDim.x, gb += ng) {
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int gg = gb + kb / TC_GROUP;
+          const bool first = (kb % TC_GROUP) == 0;
+          const int buf = gg & 1;
+          if (first && gg >= 2) {
+            // the epilogue has read this buffer's previous k-block
+            if (!mbar_wait(&acce[buf], (uint32_t)((gg >> 1) - 1) & 1u)) {
+              s_fail = 1;
+              stop = true;
+              break;
+            }
+            tc_fence_after();
+          }
+          const int s = g % TC_STAGES;
+          const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph)) {
             s_fail = 1;
+            stop = true;
             break;
           }
           tc_fence_after();
-        }
-        const int s = kb % TC_STAGES;
-        const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-        if (!mbar_wait(&full[s], ph)) {
-          s_fail = 1;
-          break;
-        }
-        tc_fence_after();
-        const uint64_t ad = umma_sdesc(smem_u32(sA + s * TC_BM * 128));
-        const uint64_t bd = umma_sdesc(smem_u32(sB + s * TC_BN * 128));
-        const uint32_t dst = tmem + (uint32_t)(buf * TC_BN);
+          const uint64_t ad = umma_sdesc(smem_u32(sA + s * TC_BM * 128));
+          const uint64_t bd = umma_sdesc(smem_u32(sB + s * TC_BN * 128));
+          const uint32_t dst = tmem + (uint32_t)(buf * TC_BN);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) umma<FP8>(dst, ad + 2 * k, bd + 2 * k, idesc, (first && k == 0) ? 0u : 1u);
-        umma_commit(&empty[s]);
-        if ((kb % TC_GROUP) == TC_GROUP - 1 || kb == nk - 1) umma_commit(&accf[buf]);
+          for (int k = 0; k < 4; ++k) umma<FP8>(dst, ad + 2 * k, bd + 2 * k, idesc, (first && k == 0) ? 0u : 1u);
+          umma_commit(&empty[s]);
+          if ((kb % TC_GROUP) == TC_GROUP - 1 || kb == nk - 1) umma_commit(&accf[buf]);
+        }
       }
     }
   } else {
     const int e = warp - 2;
     const int q = warp & 3;                  // TMEM lane quarter this warp may read
     const int h = e >> 2;                    // column half
-    const int64_t row = m0 + q * 32 + lane;
-    float acc[TC_BN / 2];
+    int gb = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, gb += ng) {
+      const int64_t m0 = (int64_t)(t % tm) * TC_BM, n0 = (int64_t)(t / tm) * TC_BN;
+      const int64_t row = m0 + q * 32 + lane;
+      float acc[TC_BN / 2];
 #pragma unroll
-    for (int i = 0; i < TC_BN / 2; ++i) acc[i] = 0.f;
-    bool ok = true;
-    for (int g = 0; g < ng; ++g) {
-      const int buf = g & 1;
-      if (!mbar_wait(&accf[buf], (uint32_t)(g >> 1) & 1u)) {
-        ok = false;
-        s_fail = 1;
-        break;
+      for (int i = 0; i < TC_BN / 2; ++i) acc[i] = 0.f;
+      bool ok = true;
+      for (int g = 0; g < ng; ++g) {
+        const int gg = gb + g;
+        const int buf = gg & 1;
+        if (!mbar_wait(&accf[buf], (uint32_t)(gg >> 1) & 1u)) {
+          ok = false;
+          s_fail = 1;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < TC_BN / 64; ++c) {
+          uint32_t r[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN + h * (TC_BN / 2) + c * 32), r);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[c * 32 + i] = __fadd_rn(acc[c * 32 + i], __uint_as_float(r[i]));
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[buf]);
       }
-      tc_fence_after();
+      if (!ok) break;
+      const float sc = row < K ? (scale ? scale[row] : 1.f) : 0.f;
 #pragma unroll
       for (int c = 0; c < TC_BN / 64; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_BN + h * (TC_BN / 2) + c * 32), r);
+        const TcCol mine = tc_col(n0 + h * (TC_BN / 2) + c * 32 + lane, nslots, list, sigma);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[c * 32 + i] = __fadd_rn(acc[c * 32 + i], __uint_as_float(r[i]));
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acce[buf]);
-    }
-    const float sc = row < K ? (scale ? scale[row] : 1.f) : 0.f;
-    if (ok && row < K) {
-#pragma unroll
-      for (int i = 0; i < TC_BN / 2; ++i) {
-        const int col = h * (TC_BN / 2) + i;
-        if (s_on[col]) Gfull[(int64_t)s_sig[col] * K + row] = acc[i] * sc * s_sigma[col];
+        for (int i = 0; i < 32; ++i) {
+          const int on = __shfl_sync(0xffffffffu, mine.on, i);
+          const int sig = __shfl_sync(0xffffffffu, mine.sig, i);
+          const float sg = __shfl_sync(0xffffffffu, mine.sigma, i);
+          if (on && row < K) Gfull[(int64_t)sig * K + row] = acc[c * 32 + i] * sc * sg;
+        }
       }
     }
   }
@@ -463,7 +514,16 @@ void tc_launch_corr(const TcOperands& ops, int64_t K, int64_t B, int64_t ldN, co
   static bool attr_kb = false;
   const int es = ops.fp8 ? 1 : 2;
   const int nkb = (int)((ldN * es + 127) / 128);   // 128-byte K-slices (TMA zero-fills the tail)
-  const dim3 grid((unsigned)((K + TC_BM - 1) / TC_BM), (unsigned)((B + TC_BN - 1) / TC_BN));
+  // persistent CTAs: at most one per SM (each holds about 200 KB of shared memory and all of TMEM)
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int64_t tiles = ((K + TC_BM - 1) / TC_BM) * ((B + TC_BN - 1) / TC_BN);
+  const dim3 grid((unsigned)std::min<int64_t>(tiles, sms));
   if (ops.promote && !ops.fp8) {
     if (!attr_kb) {
       cudaFuncSetAttribute(k_tc_corr_kb<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCP_SMEM);
