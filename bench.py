@@ -645,7 +645,7 @@ def run_config(args):
             Aty = levs[-1].op.rmatvec(y)
             lam = float(w.lam_ratio[0]) * OL.lambda_max(Aty)
             t0 = time.perf_counter()
-            r = OS.fast_l1(levs, levs[-1].atnorm, y, lam, TOL, Lip=Lip, Aty=Aty, max_iter=40 if cfg == "c5" else 100000)
+            r = OS.fast_l1(levs, levs[-1].atnorm, y, lam, TOL, Lip=Lip, Aty=Aty, max_iter=200 if cfg == "c5" else 100000)
             dt = time.perf_counter() - t0
             if r.converged:
                 cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

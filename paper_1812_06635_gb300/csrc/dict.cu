@@ -269,6 +269,48 @@ __global__ void k_kron_dense_f32(const float* __restrict__ Bf, const float* __re
   }
 }
 
+// The FP64 rung of a Kronecker dictionary: the atoms a_j = d_j sum_r B_r[:, k1] (x) C_r[:, k2]
+// evaluated in FP64 (one warp per atom).  Each entry is R products summed and scaled by d_j, so
+// its error is at most gamma_{R+1}(u64) d_j sum_r |B| |C|; eps_j bounds the norm of those errors,
+// kappa_j = ||a~_j|| (the rung's own rounding weight) and atn_j = ||a~_j|| rounded up.
+__global__ void k_kron_dense_f64(const float* __restrict__ Bf, const float* __restrict__ Cf, const double* __restrict__ d,
+                                 int R, int N1, int K1, int N2, int K2, int64_t ldN, double* __restrict__ dst,
+                                 double* __restrict__ eps, float* __restrict__ atn, double* __restrict__ kappa) {
+  int lane = threadIdx.x & 31;
+  int64_t K = (int64_t)K1 * K2, N = (int64_t)N1 * N2;
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = w; j < K; j += nw) {
+    int k1 = (int)(j / K2), k2 = (int)(j % K2);
+    double sabs = 0.0, sa = 0.0;
+    for (int64_t n = lane; n < ldN; n += 32) {
+      double v = 0.0;
+      if (n < N) {
+        int n1 = (int)(n / N2), n2 = (int)(n % N2);
+        double va = 0.0;
+        for (int r = 0; r < R; ++r) {
+          const double p = (double)Bf[((int64_t)r * N1 + n1) * K1 + k1] * (double)Cf[((int64_t)r * N2 + n2) * K2 + k2];
+          v += p;
+          va += fabs(p);
+        }
+        v *= d[j];
+        va *= fabs(d[j]);
+        sabs = fma(va, va, sabs);
+        sa = fma(v, v, sa);
+      }
+      dst[j * ldN + n] = v;
+    }
+    sabs = warp_sum(sabs);
+    sa = warp_sum(sa);
+    if (lane == 0) {
+      eps[j] = gamma_n((double)R + 3.0, U64) * sqrt(sabs) * (1.0 + 1e-12);
+      const double an = sqrt(sa) * (1.0 + 1e-13);
+      atn[j] = __double2float_ru(an);
+      kappa[j] = an;
+    }
+  }
+}
+
 // eps_j + gam kappa_j and ||a_j||, rounded up to FP32 (bounds used by FP32 device code).
 __global__ void k_round_up_f32(const double* __restrict__ eps, const double* __restrict__ kappa, double gam,
                                int64_t K, float* __restrict__ out) {
@@ -754,6 +796,30 @@ int ensure_rung64(lasso_dict* d) {
   if (d->rung64.kind >= 0) return LASSO_OK;
   if (d->exact_kind != LK_F32) return LASSO_OK;
   HostLevel& h = d->rung64;
+  if (d->is_kron) {
+    // the exact A is the FP64 Kronecker sum, whose FP32 rounding (the exact level's data) carries
+    // eps_j of a few 1e-8: enough to floor certificates near 1e-6 at small lambda.  The rung
+    // holds its own FP64 evaluation, with eps_j of FP64 rounding only.
+    HostLevel r;
+    r.kind = LK_F64;
+    r.api_kind = -1;
+    r.u = U64;
+    r.rc = 1.0;
+    int rc;
+    if ((rc = alloc(&r.data, (size_t)d->K * d->ldN * sizeof(double)))) return rc;
+    if ((rc = alloc_level_vectors(d, r))) {
+      free_level(r);
+      return rc;
+    }
+    k_kron_dense_f64<<<grid_for(d->K * 32), 256>>>(d->Bf, d->Cf, d->d, d->R, d->N1, d->K1, d->N2, d->K2, d->ldN,
+                                                   (double*)r.data, r.eps, r.atnorm, r.kappa);
+    if ((rc = finish_level(d, r))) {
+      free_level(r);
+      return rc;
+    }
+    h = r;
+    return LASSO_OK;
+  }
   h = d->exact;               // shares the FP32 data and vectors of the exact level
   h.owns_data = false;
   h.kind = LK_F32D;
@@ -1342,9 +1408,13 @@ extern "C" void lasso_dict_destroy(lasso_dict* d) {
   cudaFree(d->anorm);
   cudaFree(d->anorm32);
   if (d->rung64.kind >= 0) {
-    for (auto* e : d->rung64.epsr32) cudaFree(e);
-    cudaFree(d->rung64.kappa32);
-    cudaFree(d->rung64.eps32);
+    if (d->rung64.owns_data) {
+      free_level(d->rung64);   // the Kronecker dictionary's own FP64 rung
+    } else {
+      for (auto* e : d->rung64.epsr32) cudaFree(e);
+      cudaFree(d->rung64.kappa32);
+      cudaFree(d->rung64.eps32);
+    }
   }
   delete d;
 }

@@ -1181,16 +1181,18 @@ __device__ void pass_decide(SigState& s, const PassArgs<VT>& a, double m1_bulk, 
   s.t_inv_lam = inv_lam * (1.0 + 2.0 * U64);
 }
 
-// Saturation of the FP32 iterates on the exact level: the certificate has not improved by 2 %
-// for stall_passes passes while still above tol; the signal stops and is solved again with
-// FP64 iterates by the host.
+// Saturation of the iterates on the exact level: the certificate has not improved by 2 % for
+// max(stall_passes, passes / 16) passes while still above tol; an FP32 signal stops and is solved
+// again with FP64 iterates by the host, an FP64 second solve stops with its best certificate.
 template <typename VT>
 __device__ __forceinline__ void check_stall(SigState& s, const PassArgs<VT>& a, double cert) {
   if (a.sp.stall_passes <= 0 || s.level != a.dd.n_levels - 1 || s.act != 0 || s.pending) return;
   if (cert < 0.98 * s.best_cert) {
     s.best_cert = cert;
     s.stall = 0;
-  } else if (++s.stall >= a.sp.stall_passes && cert > a.sp.tol) {
+  } else if (++s.stall >= max(a.sp.stall_passes, s.iters / 16) && cert > a.sp.tol) {
+    // (the window grows with the pass count: ISTA's gap falls like 1 / k, so a fixed window
+    // would eventually show less than 2 % progress on a converging signal)
     s.status = LASSO_ST_SATURATED;
     s.act = 2;
   }
@@ -2480,6 +2482,11 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   // saturation of the FP32 iterates on the exact level: 200 passes without a 2 % better
   // certificate (a converging FISTA improves far faster), then the FP64 solve takes over
   pa.sp.stall_passes = sizeof(VT) == 4 && o.fp64_fallback && d->exact_kind == LK_F32 ? 200 : 0;
+  // the second solve of saturated signals returns an FP32 point, whose certificate has a floor
+  // of its own (reading of the tolerance floor): it stops on the same stall test (status
+  // LASSO_ERR_MAXITER with its best certificate) instead of running to the pass limit
+  // (FISTA only: ISTA's certificate can plateau for long stretches and still converge)
+  if (sizeof(VT) == 8 && io.point_f32 && o.algo == LASSO_FISTA) pa.sp.stall_passes = 400;
   fill_pass_args(pa, w, d);
   int corr_bps = 8;
   if constexpr (sizeof(VT) == 4) {
