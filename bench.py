@@ -16,6 +16,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -275,19 +276,36 @@ def _l2_peak_gbs():
     return best
 
 
+def _code_hash(scope):
+    """sha256 prefix of the code a kernel is compiled from, comments and blank lines left out.
+    `scope` lists files; a file with an "until" marker counts only up to it (its kernel's
+    translation unit up to the end of the kernel, where everything the kernel calls is defined)."""
+    h = hashlib.sha256()
+    for item in scope:
+        t = open(os.path.join(ROOT, item["file"]), encoding="utf-8").read()
+        if item.get("until"):
+            i = t.find(item["until"])
+            if i < 0:
+                return None
+            t = t[:i]
+        t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
+        t = re.sub(r"//[^\n]*", "", t)
+        h.update("\n".join(ln.rstrip() for ln in t.splitlines() if ln.strip()).encode())
+    return h.hexdigest()[:16]
+
+
 def _traffic(kind):
-    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if the
-    kernel source has not changed since (hash recorded with the counters)."""
+    """Per-launch DRAM bytes of the dominant kernel on this workload from the committed ncu
+    summary, if the kernel's code has not changed since (hash recorded with the counters)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p)).get(kind)
-        src = open(os.path.join(ROOT, d["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != d["sha256_16"]:
+        if _code_hash(d["scope"]) != d["code_sha256_16"]:
             return None
         return d["dram_bytes_per_launch"]
-    except (KeyError, OSError, TypeError, ValueError):
+    except (KeyError, OSError, TypeError, ValueError, AttributeError):
         return None
 
 
@@ -311,7 +329,7 @@ def _c3_roofline(kms, kbytes, klaunch, level_atoms, N):
     tf = flops / corr_s / 1e12 if corr_s > 0 else 0.0
     launches = max(1.0, klaunch[1])
     roof = {"bound": "tensor", "achieved": tf, "peak": bf16_s, "unit": "TFLOP/s", "frac": tf / bf16_s,
-            "traffic": _traffic("k_corr_pass"), "kernel": "k_corr_pass (exact-level correlation + update)",
+            "traffic": _traffic("k_corr_pass@c3"), "kernel": "k_corr_pass (exact-level correlation + update)",
             "peak_source": f"{src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
             "algorithmic_flops_per_launch": flops / launches, "avg_launch_us": 1e6 * corr_s / launches,
             "work": "2 N |A_t| flops per signal-pass on the exact level (preserved atoms only)",
@@ -329,6 +347,9 @@ def _c3_roofline(kms, kbytes, klaunch, level_atoms, N):
                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
         "kernels_GBps": {names[i]: kbytes[i] / (kms[i] * 1e-3) / 1e9 for i in range(5)
                          if kms[i] > 0 and kbytes[i] > 0}}
+    if roof["traffic"] and kbytes[1] > 0:
+        # DRAM bytes (ncu) over algorithmic bytes per launch: rows shared by signals hit in L2
+        diag["l2"]["dram_traffic_over_algorithmic"] = roof["traffic"] / (kbytes[1] / launches)
     # the whole correlation stage of a pass (every level: tensor-core GEMMs and the gather pass),
     # algorithmic work 2 N |A_t| per signal-pass on each level
     st_s = (kms[1] + kms[5]) * 1e-3

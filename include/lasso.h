@@ -187,8 +187,12 @@ typedef struct {
                                 with FP64 iterates and an FP64-accumulation rung, as final_fp64
                                 does; its outputs replace the FP32 ones.  That second solve keeps
                                 its extrapolated point (the certified one) FP32-representable, so
-                                the returned gap covers the returned FP32 x.  0: such a signal
-                                ends with LASSO_ERR_MAXITER.                                     */
+                                the returned gap covers the returned FP32 x.  With FISTA, a
+                                signal of that second solve whose certificate has not improved
+                                for max(2000, passes / 2) passes ends there with
+                                LASSO_ERR_MAXITER, its best point and certificate (an FP32 point
+                                can sit above tol for good).  0: such a signal ends with
+                                LASSO_ERR_MAXITER.                                               */
     int autotune;            /* 1 (default): before the first FP32 batch of a size class (B rounded
                                 up to a power of two), time the correlation pass for atom chunks
                                 of 64 / 128 / 256 and 4 / 8 / 16 blocks per SM on a synthetic
@@ -287,8 +291,7 @@ int lasso_lambda_max(lasso_dict* dict, const float* d_Y, int64_t B, double* d_ou
  * device (else LASSO_ERR_INVALID_ARG).
  * Device buffers: d_Y (B x N FP32, rows contiguous), d_out (B FP64).  The work is queued on
  * `stream` (a cudaStream_t; the call does not wait for it).  The first call on each device
- * looks up the scratch address with that device current; make that first call before any
- * stream capture.  Every call shares the one scratch array: calls whose work overlaps on the
+ * looks up the scratch address with that device current.  Every call shares the one scratch array: calls whose work overlaps on the
  * GPU (other streams, other threads) race and must be serialised by the caller. */
 int lasso_lambda_max_noalloc(const lasso_dict* dict, const float* d_Y, int64_t B, double* d_out,
                              void* stream);
@@ -298,7 +301,9 @@ int lasso_lambda_max_noalloc(const lasso_dict* dict, const float* d_Y, int64_t B
  * dL/dy_b = A_S u and dL/dA[:, S] += r u^T - (A_S u) x_S^T, r = y_b - A_S x_S.  lambda is held
  * fixed.  Device buffers: d_Y (B x N), d_X (B x K solution), d_G (B x K, dL/dx), outputs
  * d_dY (B x N) and d_dA (K x N atom-major, accumulated over the batch; may be NULL).  Uses
- * the exact level of a dense dictionary; supports up to 1024 nonzeros per signal. */
+ * the exact level of a dense dictionary; supports up to 1024 nonzeros per signal.  d_dA is
+ * accumulated over the signals with FP32 atomic adds in no fixed order, so its last bits can
+ * differ between runs; d_dY is deterministic. */
 int lasso_backward(lasso_dict* dict, const float* d_Y, const float* d_X, const float* d_G,
                    int64_t B, float* d_dY, float* d_dA, void* stream);
 

@@ -1182,17 +1182,21 @@ __device__ void pass_decide(SigState& s, const PassArgs<VT>& a, double m1_bulk, 
 }
 
 // Saturation of the iterates on the exact level: the certificate has not improved by 2 % for
-// max(stall_passes, passes / 16) passes while still above tol; an FP32 signal stops and is solved
-// again with FP64 iterates by the host, an FP64 second solve stops with its best certificate.
+// max(stall_passes, passes / 16) passes (FP32 iterates) or max(stall_passes, passes / 2) passes
+// (the FP64 second solve) while still above tol; an FP32 signal stops and is solved again with
+// FP64 iterates by the host, an FP64 second solve stops with its best certificate.
 template <typename VT>
 __device__ __forceinline__ void check_stall(SigState& s, const PassArgs<VT>& a, double cert) {
   if (a.sp.stall_passes <= 0 || s.level != a.dd.n_levels - 1 || s.act != 0 || s.pending) return;
   if (cert < 0.98 * s.best_cert) {
     s.best_cert = cert;
     s.stall = 0;
-  } else if (++s.stall >= max(a.sp.stall_passes, s.iters / 16) && cert > a.sp.tol) {
+  } else if (++s.stall >= max(a.sp.stall_passes, s.iters / (int)(sizeof(VT) == 8 ? 2 : 16)) && cert > a.sp.tol) {
     // (the window grows with the pass count: ISTA's gap falls like 1 / k, so a fixed window
-    // would eventually show less than 2 % progress on a converging signal)
+    // would eventually show less than 2 % progress on a converging signal; the second solve
+    // ends a signal for good, so it waits until the plateau is as long as the progress before
+    // it: a certificate stuck at the floor of its FP32 point since pass k stops near pass 2 k,
+    // while FISTA on a coherent dictionary can stall for hundreds of passes and then converge)
     s.status = LASSO_ST_SATURATED;
     s.act = 2;
   }
@@ -2486,7 +2490,7 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
   // of its own (reading of the tolerance floor): it stops on the same stall test (status
   // LASSO_ERR_MAXITER with its best certificate) instead of running to the pass limit
   // (FISTA only: ISTA's certificate can plateau for long stretches and still converge)
-  if (sizeof(VT) == 8 && io.point_f32 && o.algo == LASSO_FISTA) pa.sp.stall_passes = 400;
+  if (sizeof(VT) == 8 && io.point_f32 && o.algo == LASSO_FISTA) pa.sp.stall_passes = 2000;
   fill_pass_args(pa, w, d);
   int corr_bps = 8;
   if constexpr (sizeof(VT) == 4) {
