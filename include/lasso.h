@@ -312,11 +312,13 @@ int lasso_backward(lasso_dict* dict, const float* d_Y, const float* d_X, const f
  * B x K correlations of random operands (N terms each; signed values, and all-positive values
  * for the worst accumulation) through tcgen05, compared with an FP64 evaluation of the same
  * products.  max_rel_err: largest |error| / sum_i |a_i r_i|; max_err_over_bound: largest |error|
- * over the accumulation bound the stable test assumes (gamma_{n}(u_tc) sum_i |a_i r_i| with
- * n = N + N/k products and k-steps, times 3 in split mode; u_tc = 2^-22 for BF16 and 2^-19
- * for E4M3).  mode: 0 = BF16, 1 = E4M3, 2 = split BF16 (a1 r1 + a1 r2 + a2 r1 in one
- * accumulator).  The paper has no counterpart: it checks an assumption of this build's
- * rounding model (products treated as exact there). */
+ * over the accumulation bound the stable test assumes: gamma_n(u_tc) sum_i |a_i r_i| with
+ * n = N + N/k products and k-steps (u_tc = 2^-22 for BF16, 2^-19 for E4M3); in split mode the
+ * promoted bound (each k-block of 128 products a tensor-core chain, the k-block sums added in
+ * FP32 with round to nearest).  mode: 0 = BF16, 1 = E4M3, 2 = split BF16 (a1 r1 + a1 r2 + a2 r1
+ * with promoted accumulation, as the split level runs).  The paper has no counterpart: it checks
+ * an assumption of this build's rounding model (products treated as exact there).  Returns
+ * LASSO_ERR_INVALID_ARG for a mode outside 0-2, non-positive sizes or K * B > 2^28. */
 int lasso_tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel_err, double* max_err_over_bound);
 
 /* DIAGNOSTIC, not part of the solve path (the benchmark's roofline denominator).
