@@ -277,7 +277,8 @@ def _l2_peak_gbs():
 
 
 def _code_hash(scope):
-    """sha256 prefix of the code a kernel is compiled from, comments and blank lines left out.
+    """sha256 prefix of the code a kernel is compiled from, comments, blank lines and indentation
+    left out.
     `scope` lists files; a file with an "until" marker counts only up to it (its kernel's
     translation unit up to the end of the kernel, where everything the kernel calls is defined)."""
     h = hashlib.sha256()
@@ -290,7 +291,7 @@ def _code_hash(scope):
             t = t[:i]
         t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
         t = re.sub(r"//[^\n]*", "", t)
-        h.update("\n".join(ln.rstrip() for ln in t.splitlines() if ln.strip()).encode())
+        h.update("\n".join(ln.strip() for ln in t.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
