@@ -66,6 +66,30 @@ def _ptr(a) -> C.c_void_p:
     return C.c_void_p(a.ctypes.data)
 
 
+def device_rows(t, name: str, cols: int, dtype, rows=None, device_type: str = "cuda", device=None):
+    """Return ``t`` if it is a contiguous 2-D tensor of ``dtype`` with ``cols`` columns (and ``rows``
+    rows when given) on a ``device_type`` device (``device`` when given); raise ValueError
+    otherwise.  The library reads or writes exactly rows x cols elements through the pointer, so a
+    buffer of another shape, type or device would be overrun.  ``device_type`` is "cuda" for real
+    calls (host tests pass "cpu")."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.device.type == device_type and t.dtype == dtype and t.dim() == 2
+            and t.is_contiguous() and t.shape[1] == cols and (rows is None or t.shape[0] == rows)
+            and (device is None or t.device == device)):
+        shape = f"({'B' if rows is None else rows}, {cols})"
+        where = str(device) if device is not None else device_type
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {shape} on {where}")
+    return t
+
+
+def host_shape(a: np.ndarray, name: str, shape: tuple):
+    """Raise ValueError unless the host array ``a`` has exactly ``shape`` (the library copies that
+    many elements from its pointer)."""
+    if a.shape != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, not {a.shape}")
+    return a
+
+
 def noalloc_args(Y, out, N: int, device_type: str = "cuda"):
     """Validate the buffers of ``lasso_lambda_max_noalloc`` and return ``out`` (allocated when None).
 
@@ -187,7 +211,7 @@ class Dictionary:
     def solve(self, y, lam: float, tol: float = 1e-6, **opts):
         """One signal, host buffers.  Returns (x, rel_gap, kept, Stats); status errors raise."""
         lib = nat.load()
-        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+        y = host_shape(np.ascontiguousarray(np.asarray(y, dtype=np.float64)), "y", (self.N,))
         x = np.zeros(self.K)
         kept = np.zeros(self.K, dtype=np.int32)
         gap = C.c_double()
@@ -208,14 +232,16 @@ class Dictionary:
         """
         import torch
         lib = nat.load()
-        assert Y.is_cuda and Y.dtype == torch.float32 and Y.is_contiguous()
+        device_rows(Y, "Y", self.N, torch.float32)
         B = Y.shape[0]
         if kept is not None:
             if not (kept.is_cuda and kept.dtype == torch.uint8 and kept.is_contiguous()
                     and tuple(kept.shape) == (B, self.K) and kept.device == Y.device):
                 raise ValueError(f"kept must be a contiguous CUDA uint8 tensor of shape ({B}, {self.K})")
             opts["kept_mask"] = kept.data_ptr()
-        lam = lambdas.to(device=Y.device, dtype=torch.float64).contiguous()
+        lam = torch.as_tensor(lambdas, dtype=torch.float64).to(device=Y.device).contiguous()
+        if lam.dim() != 1 or lam.numel() != B:
+            raise ValueError(f"lambdas must hold one value per signal ({B}), not shape {tuple(lam.shape)}")
         X = torch.empty((B, self.K), dtype=torch.float32, device=Y.device)
         gaps = torch.empty(B, dtype=torch.float64, device=Y.device)
         status = torch.empty(B, dtype=torch.int32, device=Y.device)
@@ -233,8 +259,11 @@ class Dictionary:
         uint8 array (B x K, C-contiguous) that receives the preserved sets at exit."""
         lib = nat.load()
         Y = np.ascontiguousarray(np.asarray(Y, dtype=np.float32))
-        lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+        if Y.ndim != 2:
+            raise ValueError(f"Y must be a B x {self.N} array, not shape {Y.shape}")
         B = Y.shape[0]
+        host_shape(Y, "Y", (B, self.N))
+        lam = host_shape(np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64)), "lambdas", (B,))
         if kept is not None:
             if not (isinstance(kept, np.ndarray) and kept.dtype == np.uint8 and kept.flags.c_contiguous
                     and kept.shape == (B, self.K)):
@@ -252,6 +281,7 @@ class Dictionary:
 
     def lambda_max(self, Y):
         import torch
+        device_rows(Y, "Y", self.N, torch.float32)
         B = Y.shape[0]
         out = torch.empty(B, dtype=torch.float64, device=Y.device)
         s = torch.cuda.current_stream(Y.device)
@@ -277,11 +307,14 @@ class Dictionary:
     def backward(self, Y, X, G, want_dA: bool = True):
         """(dL/dY (B x N), dL/dA (K x N atom-major, summed over the batch) or None) for dL/dX = G."""
         import torch
+        device_rows(Y, "Y", self.N, torch.float32)
         B = Y.shape[0]
+        X = device_rows(X.contiguous(), "X", self.K, torch.float32, rows=B, device=Y.device)
+        G = device_rows(G.contiguous(), "G", self.K, torch.float32, rows=B, device=Y.device)
         dY = torch.empty_like(Y)
         dA = torch.zeros((self.K, self.N), dtype=torch.float32, device=Y.device) if want_dA else None
         s = torch.cuda.current_stream(Y.device)
-        nat.check(nat.load().lasso_backward(self._h, _ptr(Y), _ptr(X.contiguous()), _ptr(G.contiguous()), B, _ptr(dY),
+        nat.check(nat.load().lasso_backward(self._h, _ptr(Y), _ptr(X), _ptr(G), B, _ptr(dY),
                                             _ptr(dA), C.c_void_p(s.cuda_stream)), "lasso_backward")
         return dY, dA
 
