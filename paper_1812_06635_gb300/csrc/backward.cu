@@ -174,7 +174,10 @@ extern "C" int lasso_backward(lasso_dict* d, const float* d_Y, const float* d_X,
   }
   int mmax = 1;
   for (int32_t c : hc) mmax = std::max(mmax, (int)c);
-  if (mmax > 1024) return LASSO_ERR_UNSUPPORTED;
+  if (mmax > 1024) {
+    set_last_error("lasso_backward: a signal's support exceeds 1024 atoms", __FILE__, __LINE__);
+    return LASSO_ERR_UNSUPPORTED;
+  }
   int32_t* Sbuf = nullptr;
   double *Mbuf = nullptr, *vbuf = nullptr;
   if (cudaMalloc(&Sbuf, (size_t)B * mmax * 4) != cudaSuccess ||

@@ -988,7 +988,10 @@ extern "C" int lasso_dict_create_dense(const void* A, lasso_dtype dt, int64_t N,
   *out = nullptr;
   if (!A || N <= 0 || K <= 0 || (dt != LASSO_F64 && dt != LASSO_F32)) return LASSO_ERR_INVALID_ARG;
   if (atom_major ? ld < N : ld < K) return LASSO_ERR_INVALID_ARG;
-  if (N > (1 << 24) || K > (1 << 30)) return LASSO_ERR_UNSUPPORTED;
+  if (N > (1 << 24) || K > (1 << 30)) {
+    set_last_error("lasso_dict_create_dense: N above 2^24 or K above 2^30", __FILE__, __LINE__);
+    return LASSO_ERR_UNSUPPORTED;
+  }
   lasso_dict* d = new lasso_dict();
   cudaGetDevice(&d->device);
   d->N = N;
@@ -1384,7 +1387,10 @@ extern "C" int lasso_dict_level_host(const lasso_dict* d, int level, double* eps
   const HostLevel& h = level == (int)d->approx.size() ? d->exact : d->approx[level];
   if (eps_host) LASSO_CUDA_TRY(cudaMemcpy(eps_host, h.eps, d->K * 8, cudaMemcpyDeviceToHost));
   if (atoms_host) {
-    if (level_structured(h.kind)) return LASSO_ERR_UNSUPPORTED;
+    if (level_structured(h.kind)) {
+      set_last_error("lasso_dict_level_host: a structured level has no dense atoms to copy", __FILE__, __LINE__);
+      return LASSO_ERR_UNSUPPORTED;
+    }
     double* tmp = nullptr;
     int rc = alloc((void**)&tmp, (size_t)d->K * d->N * 8);
     if (rc) return rc;

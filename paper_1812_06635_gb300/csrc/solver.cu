@@ -2468,7 +2468,10 @@ static int run_solve(lasso_dict* d, Workspace* w, const SolveIO& io, lasso_stats
     has_faust |= pa.dd.lv[l].kind == LK_FAUST;
     if (pa.dd.lv[l].kind == LK_KRON) rmax = std::max(rmax, pa.dd.lv[l].R);
   }
-  if (has_kron && B * rmax > 65535) return LASSO_ERR_UNSUPPORTED;
+  if (has_kron && B * rmax > 65535) {
+    set_last_error("Kronecker levels: signals x terms above 65535 in one batch", __FILE__, __LINE__);
+    return LASSO_ERR_UNSUPPORTED;
+  }
   pa.sp.tol = io.tol;
   pa.sp.Gamma = o.Gamma;
   pa.sp.tau = o.tau;
@@ -2849,7 +2852,10 @@ static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
   if (io.opts.rule < LASSO_RULE_GAP || io.opts.rule > LASSO_RULE_STATIC || io.opts.algo < LASSO_FISTA ||
       io.opts.algo > LASSO_ISTA)
     return LASSO_ERR_INVALID_ARG;
-  if (d->ldN > 24576) return LASSO_ERR_UNSUPPORTED;
+  if (d->ldN > 24576) {
+    set_last_error("solve: signals longer than 24576 (padded) entries", __FILE__, __LINE__);
+    return LASSO_ERR_UNSUPPORTED;
+  }
   if (!d->prepared) {
     int rc = dict_prepare(d, 0.0);
     if (rc) return rc;
