@@ -22,7 +22,9 @@
  *    of the returned point for the original problem over the whole dictionary (rounding of
  *    every kernel is folded in).  A signal stops when this bound is <= tol at the exact level.
  *  - Every call returns a status (lasso_status) and never aborts; on error the outputs are
- *    left as documented per call.  lasso_strerror() gives a message.
+ *    left as documented per call.  lasso_strerror() gives a message; when the most recent
+ *    status-returning call on the same thread recorded a detail (the limit it refused, the
+ *    CUDA call that failed), the message carries it.
  *  - Pointers named *_host are host memory; pointers named d_* are device memory of the
  *    current CUDA device.  The library owns every lasso_dict it creates.
  *  - Thread safety: a lasso_dict may be used by one call at a time.

@@ -157,8 +157,13 @@ k_backward(LevelDev L, int N, int64_t K, int mmax, const float* __restrict__ Y, 
 
 using namespace lasso;
 
+namespace lasso {
+void clear_last_error();   // capi.cu
+}  // namespace lasso
+
 extern "C" int lasso_backward(lasso_dict* d, const float* d_Y, const float* d_X, const float* d_G, int64_t B,
                               float* d_dY, float* d_dA, void* stream) {
+  lasso::clear_last_error();
   if (!d || !d_Y || !d_X || !d_G || !d_dY || B <= 0) return LASSO_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   int32_t* counts = nullptr;

@@ -982,8 +982,13 @@ int dict_prepare(lasso_dict* d, double L_override) {
 
 using namespace lasso;
 
+namespace lasso {
+void clear_last_error();   // capi.cu
+}  // namespace lasso
+
 extern "C" int lasso_dict_create_dense(const void* A, lasso_dtype dt, int64_t N, int64_t K, int64_t ld,
                                        int atom_major, int normalize, int host_ptr, lasso_dict** out) {
+  lasso::clear_last_error();
   if (!out) return LASSO_ERR_INVALID_ARG;
   *out = nullptr;
   if (!A || N <= 0 || K <= 0 || (dt != LASSO_F64 && dt != LASSO_F32)) return LASSO_ERR_INVALID_ARG;
@@ -1057,6 +1062,7 @@ fail:
 
 extern "C" int lasso_dict_create_kron(const float* B, const float* C, int R, int N1, int K1, int N2, int K2,
                                       int normalize, int host_ptr, lasso_dict** out) {
+  lasso::clear_last_error();
   if (!out) return LASSO_ERR_INVALID_ARG;
   *out = nullptr;
   if (!B || !C || R <= 0 || N1 <= 0 || K1 <= 0 || N2 <= 0 || K2 <= 0 || R > 64) return LASSO_ERR_INVALID_ARG;
@@ -1117,6 +1123,7 @@ fail:
 }
 
 extern "C" int lasso_dict_add_level(lasso_dict* d, lasso_level_kind kind, int param) {
+  lasso::clear_last_error();
   if (!d || (int)d->approx.size() + 1 >= MAX_LEVELS - 1) return LASSO_ERR_INVALID_ARG;
   HostLevel h;
   h.api_kind = kind;
@@ -1202,6 +1209,7 @@ double* faust_explicit(const HostLevel& h, int64_t K, int64_t ld, int absval, do
 
 extern "C" int lasso_dict_add_level_faust(lasso_dict* d, int J, const int64_t* dims, const int64_t* indptr,
                                           const int32_t* indices, const float* values) {
+  lasso::clear_last_error();
   if (!d || (int)d->approx.size() + 1 >= MAX_LEVELS - 1) return LASSO_ERR_INVALID_ARG;
   if (J < 1 || J > 16 || !dims || !indptr || !indices || !values) return LASSO_ERR_INVALID_ARG;
   for (int f = 0; f <= J; ++f)
@@ -1345,6 +1353,7 @@ extern "C" int lasso_dict_add_level_faust(lasso_dict* d, int J, const int64_t* d
 }
 
 extern "C" int lasso_dict_set_rc(lasso_dict* d, int level, double rc) {
+  lasso::clear_last_error();
   if (!d || level < 0 || level > (int)d->approx.size() || !(rc > 0.0)) return LASSO_ERR_INVALID_ARG;
   HostLevel& h = level == (int)d->approx.size() ? d->exact : d->approx[level];
   h.rc = rc;
@@ -1353,11 +1362,13 @@ extern "C" int lasso_dict_set_rc(lasso_dict* d, int level, double rc) {
 }
 
 extern "C" int lasso_dict_prepare(lasso_dict* d, double L_override) {
+  lasso::clear_last_error();
   if (!d) return LASSO_ERR_INVALID_ARG;
   return dict_prepare(d, L_override);
 }
 
 extern "C" int lasso_dict_info(const lasso_dict* d, lasso_dict_info_t* info) {
+  lasso::clear_last_error();
   if (!d || !info) return LASSO_ERR_INVALID_ARG;
   memset(info, 0, sizeof(*info));
   info->N = d->N;
@@ -1383,6 +1394,7 @@ __global__ void k_level_to_f64(LevelDev L, int64_t N, int64_t K, double* __restr
 }
 
 extern "C" int lasso_dict_level_host(const lasso_dict* d, int level, double* eps_host, double* atoms_host) {
+  lasso::clear_last_error();
   if (!d || level < 0 || level > (int)d->approx.size()) return LASSO_ERR_INVALID_ARG;
   const HostLevel& h = level == (int)d->approx.size() ? d->exact : d->approx[level];
   if (eps_host) LASSO_CUDA_TRY(cudaMemcpy(eps_host, h.eps, d->K * 8, cudaMemcpyDeviceToHost));

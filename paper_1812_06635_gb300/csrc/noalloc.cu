@@ -111,8 +111,13 @@ static LevelDev exact_level_rows(const lasso_dict* d) {
   return L;
 }
 
+namespace lasso {
+void clear_last_error();   // capi.cu
+}  // namespace lasso
+
 extern "C" int lasso_lambda_max_noalloc(const lasso_dict* d, const float* d_Y, int64_t B, double* d_out,
                                         void* stream) {
+  lasso::clear_last_error();
   if (!d || !d_Y || !d_out || B <= 0) {
     set_last_error("lasso_lambda_max_noalloc: null dictionary or buffer, or B <= 0", __FILE__, __LINE__);
     return LASSO_ERR_INVALID_ARG;

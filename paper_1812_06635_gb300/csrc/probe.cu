@@ -43,7 +43,12 @@ __global__ void __launch_bounds__(256) k_l2_read(const float4* __restrict__ buf,
 
 using namespace lasso;
 
+namespace lasso {
+void clear_last_error();   // capi.cu
+}  // namespace lasso
+
 extern "C" int lasso_probe_l2_read(int64_t bytes, int rounds, double* gbs) {
+  lasso::clear_last_error();
   if (!gbs || bytes < (1 << 20) || bytes > ((int64_t)96 << 20) || rounds < 1 || rounds > 1000)
     return LASSO_ERR_INVALID_ARG;
   int dev = 0, sms = 0;

@@ -2875,9 +2875,14 @@ static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
   return fp64_fallback(d, w, io, stats);
 }
 
+namespace lasso {
+void clear_last_error();   // capi.cu
+}  // namespace lasso
+
 extern "C" int lasso_solve_batch(lasso_dict* d, const float* d_Y, const double* d_lambdas, int64_t B, double tol,
                                  const lasso_opts* opts, float* d_X, double* d_gaps, int32_t* d_status,
                                  int32_t* d_iters, void* stream, lasso_stats* stats) {
+  lasso::clear_last_error();
   if (!d_Y || !d_lambdas || !d_X) return LASSO_ERR_INVALID_ARG;
   SolveIO io;
   io.Yf = d_Y;
@@ -2897,6 +2902,7 @@ extern "C" int lasso_solve_batch(lasso_dict* d, const float* d_Y, const double* 
 extern "C" int lasso_solve_batch_host(lasso_dict* d, const float* Y, const double* lambdas, int64_t B, double tol,
                                       const lasso_opts* opts, float* X, double* gaps, int32_t* status,
                                       lasso_stats* stats) {
+  lasso::clear_last_error();
   if (!d || !Y || !lambdas || !X || B <= 0) return LASSO_ERR_INVALID_ARG;
   float *dY = nullptr, *dX = nullptr;
   double *dl = nullptr, *dg = nullptr;
@@ -2936,6 +2942,7 @@ extern "C" int lasso_solve_batch_host(lasso_dict* d, const float* Y, const doubl
 
 extern "C" int lasso_solve(lasso_dict* d, const double* y, double lambda, double tol, const lasso_opts* opts,
                            double* x, double* gap, int32_t* kept, int64_t* n_kept, lasso_stats* stats) {
+  lasso::clear_last_error();
   if (!d || !y || !x) return LASSO_ERR_INVALID_ARG;
   double *dy = nullptr, *dl = nullptr;
   if (cudaMalloc(&dy, d->N * 8) != cudaSuccess || cudaMalloc(&dl, 8) != cudaSuccess) {
@@ -3025,6 +3032,7 @@ static int run_lambda_max(lasso_dict* d, Workspace* w, const float* Y, int64_t B
 }
 
 extern "C" int lasso_lambda_max(lasso_dict* d, const float* d_Y, int64_t B, double* d_out, void* stream) {
+  lasso::clear_last_error();
   if (!d || !d_Y || !d_out || B <= 0) return LASSO_ERR_INVALID_ARG;
   const bool vt_double = d->exact_kind == LK_F64;
   Workspace* w = nullptr;

@@ -684,8 +684,13 @@ int tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel, doub
 
 }  // namespace lasso
 
+namespace lasso {
+void clear_last_error();   // capi.cu
+}  // namespace lasso
+
 extern "C" int lasso_tc_selftest(int mode, int64_t K, int64_t N, int64_t B, double* max_rel_err,
                                  double* max_err_over_bound) {
+  lasso::clear_last_error();
   if (K <= 0 || N <= 0 || B <= 0 || K * B > (int64_t)1 << 28 || mode < 0 || mode > 2) return LASSO_ERR_INVALID_ARG;
   return lasso::tc_selftest(mode, K, N, B, max_rel_err, max_err_over_bound);
 }

@@ -49,6 +49,21 @@ def test_host_only_calls(lib):
     assert lib.lasso_solve(None, None, 1.0, 1e-6, None, None, None, None, None, None) == -1
 
 
+def test_messages_carry_the_refused_limit_of_the_latest_call(lib):
+    """A refusal that records a detail shows it in lasso_strerror; the next call starts clean,
+    so a later refusal without a detail shows the plain message (no stale text)."""
+    import numpy as np
+    h = C.c_void_p()
+    buf = np.zeros(4, dtype=np.float32)
+    p = buf.ctypes.data_as(C.c_void_p)
+    code = lib.lasso_dict_create_dense(p, 1, (1 << 24) + 1, 1, (1 << 24) + 1, 1, 0, 1, C.byref(h))
+    assert code == -6 and not h.value
+    msg = lib.lasso_strerror(code).decode()
+    assert msg.startswith("unsupported size or option") and "2^24" in msg, msg
+    assert lib.lasso_dict_create_dense(p, 1, 0, 1, 1, 1, 0, 1, C.byref(h)) == -1
+    assert lib.lasso_strerror(-1).decode() == "invalid argument"
+
+
 def test_library_is_built_for_sm_103a_only():
     from paper_1812_06635_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
