@@ -232,3 +232,56 @@ def test_fp32_residual_models(nnz):
             else:
                 bound = gamma(nnz + 4) * skz + 2.0 * U * nr
             assert err <= bound, (d2, err, bound)
+
+
+U64 = 2.0 ** -53
+
+
+def _gamma64(n):
+    return n * U64 / (1.0 - n * U64)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fp64_kronecker_rung_bound(seed):
+    """The FP64 rung of a Kronecker dictionary forms a_j = d_j sum_r b_r (x) c_r entry by entry:
+    FP64 products of FP32 factor entries (exact), summed over r in order, then times d_j (FP64).
+    Its eps_j claims ||a^_j - a_j|| <= gamma_{R+3}(2^-53) ||d_j sum_r |b_r (x) c_r| ||, and kappa_j
+    bounds ||a^_j||.  Checked against exact rational arithmetic, with factor entries of both signs
+    (cancelling terms) and spread exponents."""
+    from fractions import Fraction
+    rng = np.random.default_rng(100 + seed)
+    R, N1, K1, N2, K2 = 5, 3, 4, 4, 3
+    Bf = (rng.standard_normal((R, N1, K1)) * 2.0 ** rng.integers(-6, 6, (R, N1, K1))).astype(np.float32)
+    Cf = (rng.standard_normal((R, N2, K2)) * 2.0 ** rng.integers(-6, 6, (R, N2, K2))).astype(np.float32)
+    dcol = rng.uniform(0.5, 2.0, K1 * K2)
+    worst = 0.0
+    for j in range(K1 * K2):
+        k1, k2 = divmod(j, K2)
+        d = float(dcol[j])
+        err2, norm2 = Fraction(0), Fraction(0)
+        sabs, sa = 0.0, 0.0
+        for n in range(N1 * N2):
+            n1, n2 = divmod(n, N2)
+            v, va = 0.0, 0.0
+            exact = Fraction(0)
+            for r in range(R):
+                b, c = float(Bf[r, n1, k1]), float(Cf[r, n2, k2])
+                p = b * c                                  # exact: 24 + 24 significant bits
+                assert Fraction(p) == Fraction(b) * Fraction(c)
+                v += p
+                va += abs(p)
+                exact += Fraction(b) * Fraction(c)
+            v *= d
+            va *= abs(d)
+            sabs += va * va
+            sa += v * v
+            err2 += (Fraction(v) - Fraction(d) * exact) ** 2
+            norm2 += Fraction(v) ** 2
+        eps = _gamma64(R + 3.0) * np.sqrt(sabs) * (1.0 + 1e-12)
+        kappa = np.sqrt(sa) * (1.0 + 1e-13)
+        err = float(err2) ** 0.5
+        assert err <= eps, (j, err, eps)
+        # kappa_j >= ||a^_j||, compared in squares to avoid a rounded square root
+        assert Fraction(kappa) ** 2 >= norm2, j
+        worst = max(worst, err / eps)
+    assert worst > 0.0          # the sums did round somewhere: the check is not vacuous
