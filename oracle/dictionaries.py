@@ -258,6 +258,23 @@ def fp8_quantize(A):
     return q * s[None, :], q, s
 
 
+def split_bf16(A):
+    """The split BF16 pair of an FP32 dictionary, an approximate dictionary in the sense of
+    Section III: entrywise a1 = bf16(a), a2 = bf16(a - a1), approximation a~ = a1 + a2.
+
+    a - a1 is exact in FP32: a1 is a rounding of a, so the difference lies on a's own grid with
+    at most 16 significant bits.  A is N x K (atoms as columns).  Returns (a1, a2, eps): a1 and
+    a2 as FP64 arrays of the BF16 values, and eps_j = ||a_j - a1_j - a2_j||_2 from the exact
+    entrywise remainders.
+    """
+    a = to_f32(A)
+    a1 = bf16_round(a.astype(np.float32))
+    r = a - a1
+    a2 = bf16_round(r.astype(np.float32))
+    e = r - a2
+    return a1, a2, np.sqrt(np.sum(e * e, axis=0))
+
+
 # ----------------------------------------------------------------------------- ladder
 
 @dataclass

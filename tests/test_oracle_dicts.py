@@ -38,6 +38,31 @@ def test_e4m3_matches_torch_cast_in_range_and_saturates():
     np.testing.assert_array_equal(D.e4m3_round(big), np.sign(big) * 448.0)
 
 
+def test_split_bf16_pair():
+    """a1 and a2 are torch's BF16 casts of a and of the exact remainder a - a1. Each BF16 rounding
+    keeps 8 significant bits, so what both leave is at most 2^-16 |a| entrywise and
+    eps_j <= 2^-16 ||a_j||. Entries of at most 16 significant bits split exactly (eps = 0)."""
+    v = _f32_samples(60000, 3).reshape(300, 200)
+    a1, a2, eps = D.split_bf16(v)
+    t = torch.from_numpy(v)
+    ref1 = t.to(torch.bfloat16).to(torch.float64)
+    np.testing.assert_array_equal(a1, ref1.numpy())
+    rem = t.to(torch.float64) - ref1
+    assert torch.equal(rem.to(torch.float32).to(torch.float64), rem)          # the remainder is an FP32 value
+    np.testing.assert_array_equal(a2, rem.to(torch.float32).to(torch.bfloat16).to(torch.float64).numpy())
+    a = v.astype(np.float64)
+    e = a - a1 - a2
+    assert np.all(np.abs(e) <= 2.0 ** -16 * np.abs(a))
+    np.testing.assert_allclose(eps, np.linalg.norm(e, axis=0), rtol=1e-14)
+    assert np.all(eps <= 2.0 ** -16 * np.linalg.norm(a, axis=0))
+    assert np.any(eps > 0)
+    # 16 significant bits (the implicit one and 15 stored): a1 + a2 == a
+    v16 = (v.view(np.uint32) & np.uint32(0xFFFFFF00)).view(np.float32)
+    b1, b2, eps16 = D.split_bf16(v16)
+    np.testing.assert_array_equal(b1 + b2, v16.astype(np.float64))
+    assert np.all(eps16 == 0.0)
+
+
 def test_fp8_atom_scaled_copy():
     A = S.dense_small(N=64, K=100, n_signals=1).A
     At, q, s = D.fp8_quantize(A)

@@ -107,6 +107,14 @@ def _matvec_wrong_order(self, x, idx=None):
     return v
 
 
+def _split_without_remainder(A):
+    a = D.to_f32(A)
+    a1 = D.bf16_round(a.astype(np.float32))
+    a2 = D.bf16_round((a - a1).astype(np.float32)) * 0.5       # the second part halved
+    e = a - a1 - a2
+    return a1, a2, np.sqrt(np.sum(e * e, axis=0))
+
+
 REGION_CASES = [
     (G, "C_pq", _C_pq_flipped, lambda: TR.test_C_pq_against_extreme_points(3, 3.0)),
     (G, "zone_sphere_test", _zone_test_without_eps_term,
@@ -116,6 +124,7 @@ REGION_CASES = [
     (D.FaustDict, "_apply_t", staticmethod(_apply_t_through_rows),
      lambda: TD.test_faust_operator_against_explicit_product((6, 9, 13))),
     (D.FaustDict, "matvec", _matvec_wrong_order, lambda: TD.test_faust_operator_against_explicit_product((6, 9, 13))),
+    (D, "split_bf16", _split_without_remainder, lambda: TD.test_split_bf16_pair()),
 ]
 
 
