@@ -334,7 +334,9 @@ def _c3_roofline(kms, kbytes, klaunch, level_atoms, N):
             "peak_source": f"{src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
             "algorithmic_flops_per_launch": flops / launches, "avg_launch_us": 1e6 * corr_s / launches,
             "work": "2 N |A_t| flops per signal-pass on the exact level (preserved atoms only)",
-            "kernel_share": {names[i]: kms[i] / max(1e-9, kms.sum()) for i in range(6) if kms[i] > 0}}
+            "kernel_share": {names[i]: kms[i] / max(1e-9, kms.sum()) for i in range(6) if kms[i] > 0},
+            "why_this_kernel": "the correlation, the step the C3 measurement grades; the residual pass and the "
+                               "evaluation + screening group take similar shares of the step (kernel_share)"}
     gbps = kbytes[1] / corr_s / 1e9 if corr_s > 0 else 0.0
     l2 = _l2_peak_gbs()
     diag = {
