@@ -254,6 +254,8 @@ int lasso_solve(lasso_dict* dict, const double* y_host, double lambda, double to
  * buffers: d_Y (B x N FP32, row b = y_b), d_lambdas (B FP64), d_X (B x K FP32 output),
  * d_gaps (B FP64 output), d_status (B int32 output: lasso_status per signal), d_iters (B int32
  * output, may be NULL); opts->kept_mask optionally receives the preserved sets.
+ * 1 <= B <= 65535 and N <= 24576 after padding (LASSO_ERR_UNSUPPORTED, with the limit in the
+ * message, beyond that).
  * Synchronisation: the passes run as a CUDA graph of opts->passes_per_sync passes, replayed
  * until every signal has stopped; between replays the host reads a 4-byte count of finished
  * signals from the device (one stream synchronisation per replay), and the stream is
@@ -278,7 +280,8 @@ int lasso_solve_batch_host(lasso_dict* dict, const float* Y_host, const double* 
 
 /* lambda_max = ||A^T y||_inf of B signals (eq:DefLMax: for lambda >= lambda_max the solution is
  * x = 0).  Device buffers: d_Y (B x N FP32), d_out (B FP64 output); exact level, error-free
- * products; queued on `stream` (a cudaStream_t).  May allocate its workspace on first use. */
+ * products; queued on `stream` (a cudaStream_t).  May allocate its workspace on first use.
+ * 1 <= B <= 65535 (LASSO_ERR_UNSUPPORTED beyond). */
 int lasso_lambda_max(lasso_dict* dict, const float* d_Y, int64_t B, double* d_out, void* stream);
 
 /* Same values as lasso_lambda_max, for callers that cannot allocate device memory (their

@@ -2856,6 +2856,10 @@ static int solve_common(lasso_dict* d, SolveIO& io, lasso_stats* stats) {
     set_last_error("solve: signals longer than 24576 (padded) entries", __FILE__, __LINE__);
     return LASSO_ERR_UNSUPPORTED;
   }
+  if (io.B > 65535) {   // per-signal kernels index the batch by gridDim.y
+    set_last_error("solve: more than 65535 signals in one call", __FILE__, __LINE__);
+    return LASSO_ERR_UNSUPPORTED;
+  }
   if (!d->prepared) {
     int rc = dict_prepare(d, 0.0);
     if (rc) return rc;
@@ -2904,6 +2908,10 @@ extern "C" int lasso_solve_batch_host(lasso_dict* d, const float* Y, const doubl
                                       lasso_stats* stats) {
   lasso::clear_last_error();
   if (!d || !Y || !lambdas || !X || B <= 0) return LASSO_ERR_INVALID_ARG;
+  if (B > 65535) {
+    set_last_error("solve: more than 65535 signals in one call", __FILE__, __LINE__);
+    return LASSO_ERR_UNSUPPORTED;
+  }
   float *dY = nullptr, *dX = nullptr;
   double *dl = nullptr, *dg = nullptr;
   int32_t* ds = nullptr;
@@ -3034,6 +3042,10 @@ static int run_lambda_max(lasso_dict* d, Workspace* w, const float* Y, int64_t B
 extern "C" int lasso_lambda_max(lasso_dict* d, const float* d_Y, int64_t B, double* d_out, void* stream) {
   lasso::clear_last_error();
   if (!d || !d_Y || !d_out || B <= 0) return LASSO_ERR_INVALID_ARG;
+  if (B > 65535) {
+    set_last_error("lambda_max: more than 65535 signals in one call", __FILE__, __LINE__);
+    return LASSO_ERR_UNSUPPORTED;
+  }
   const bool vt_double = d->exact_kind == LK_F64;
   Workspace* w = nullptr;
   if (trace_steps()) fprintf(stderr, "[lasso trace] lmax: enter (stream %p)\n", stream);
