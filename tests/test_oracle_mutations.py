@@ -6,9 +6,11 @@ a missing clip) and runs a pin from ``test_oracle_problem``; the pin must raise.
 import numpy as np
 import pytest
 
+import test_oracle_backward as TB
 import test_oracle_dicts as TD
 import test_oracle_problem as P
 import test_oracle_regions as TR
+from oracle import backward as OB
 from oracle import dictionaries as D
 from oracle import lasso as L
 from oracle import regions as G
@@ -115,6 +117,54 @@ def _split_without_remainder(A):
     return a1, a2, np.sqrt(np.sum(e * e, axis=0))
 
 
+def _bf16_truncating(a):
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    bits = f.view(np.uint32).astype(np.uint64) & 0xFFFF0000          # chops instead of rounding
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+_e4m3_right = D.e4m3_round
+
+
+def _e4m3_ties_away(v):
+    v = np.asarray(v, dtype=np.float64)
+    up = _e4m3_right(v * (1.0 + 2.0 ** -20))                         # nudges every tie outwards
+    return np.where(np.abs(v) > 0, up, 0.0)
+
+
+def _kron_eps_without_scale(Bf, Cf, d, R_keep):
+    tb, tc = Bf[R_keep:], Cf[R_keep:]
+    GB = np.einsum("rnk,snk->rsk", tb, tb)
+    GC = np.einsum("rnk,snk->rsk", tc, tc)
+    return np.sqrt(np.maximum(np.einsum("rsa,rsb->ab", GB, GC).reshape(-1), 0.0))   # d_j dropped
+
+
+def _kron_matvec_transposed_c(self, x, idx=None):
+    full = np.zeros(self.K)
+    if idx is None:
+        full[:] = x
+    else:
+        full[idx] = x
+    X = (self.d * full).reshape(self.K1, self.K2)
+    out = np.zeros((self.N1, self.N2))
+    for r in range(self.R):
+        out += self.Bf[r] @ X @ self.Cf[r][::-1].T                  # rows of C_r in reverse order
+    return out.reshape(-1)
+
+
+def _adjoint_sign_slip(A, y, x, g):
+    dy, dA = _adjoint_right(A, y, x, g)
+    S = np.flatnonzero(x)
+    if S.size:
+        AS = A[:, S]
+        u = np.linalg.solve(AS.T @ AS, g[S])
+        dA[:, S] = np.outer(y - AS @ x[S], u) + np.outer(AS @ u, x[S])   # + instead of -
+    return dy, dA
+
+
+_adjoint_right = OB.support_adjoint
+
+
 REGION_CASES = [
     (G, "C_pq", _C_pq_flipped, lambda: TR.test_C_pq_against_extreme_points(3, 3.0)),
     (G, "zone_sphere_test", _zone_test_without_eps_term,
@@ -125,6 +175,12 @@ REGION_CASES = [
      lambda: TD.test_faust_operator_against_explicit_product((6, 9, 13))),
     (D.FaustDict, "matvec", _matvec_wrong_order, lambda: TD.test_faust_operator_against_explicit_product((6, 9, 13))),
     (D, "split_bf16", _split_without_remainder, lambda: TD.test_split_bf16_pair()),
+    (D, "bf16_round", _bf16_truncating, lambda: TD.test_bf16_matches_torch_cast()),
+    (D, "e4m3_round", _e4m3_ties_away, lambda: TD.test_e4m3_matches_torch_cast_in_range_and_saturates()),
+    (D, "kron_truncation_eps_gram", _kron_eps_without_scale,
+     lambda: TD.test_kron_truncation_eps_gram_equals_column_differences()),
+    (D.KronDict, "matvec", _kron_matvec_transposed_c, lambda: TD.test_kron_operator_against_explicit_kron()),
+    (OB, "support_adjoint", _adjoint_sign_slip, lambda: TB.test_adjoint_matches_central_differences()),
 ]
 
 
